@@ -1,0 +1,360 @@
+"""Benchmark of the GB300 connected-components library (adaptive Hook-Compress).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid|er|rmat] [--impl ours|reference]
+
+One step = one complete labelling of the workload graph (pi init, every Atomic-Hook
+segment and every Multi-Jump) through the C ABI, with the graph already resident in
+HBM. Between steps L2 is flushed by writing a 256 MiB buffer (outside the timed events).
+Prints ONE JSON line on rank 0.
+
+Workloads (seeded synthetic graphs, generated on the host before timing):
+  grid : road-like 4096 x 4096 lattice, each edge kept with p = 0.9, int32 CSR (default)
+  er   : Erdos-Renyi, V = 100,000, 1,000,000 drawn edges, int32 CSR
+  rmat : R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), permuted IDs, int64 offsets
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "CC edges/sec and % of HBM roofline at 1 GB300"
+UNIT = "edges/s"
+FLUSH_BYTES = 256 << 20
+DEFAULT_PEAK_GBS = 6674.5  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+
+WORKLOADS = {
+    "grid": ("grid4096_p0.9", lambda: gen.workload_grid_4096(seed=1)),
+    "er": ("er_V100000_E1000000", lambda: gen.workload_er_100k(seed=1)),
+    "rmat": ("rmat26_ef16", lambda: gen.workload_rmat_26(seed=1)),
+}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return DEFAULT_PEAK_GBS, "fallback"
+
+
+def algorithmic_bytes(g) -> int:
+    """Compulsory bytes of one labelling: col_idx read once, row_ptr read once, labels written once."""
+    off = g.row_ptr.dtype.itemsize
+    return 4 * g.nnz + off * (g.n_vertices + 1) + 4 * g.n_vertices
+
+
+# ------------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- reference
+
+def cpu_oracle_rate(g, budget_s: float = 12.0, max_runs: int = 1000):
+    """The oracle (union-find, single thread) timed on this host on the whole workload graph,
+    repeated until `budget_s` of CPU time is spent. Returns (edges/s, runs, labels)."""
+    import oracle
+    rp64 = g.row_ptr.astype(np.int64)
+    labels = None
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < max_runs:
+        t0 = time.perf_counter()
+        labels, _ = oracle.labels_uf_csr(rp64, g.col)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end:
+            break
+    return g.n_edges / statistics.mean(times), len(times), labels
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    name, make = WORKLOADS[args.workload]
+    g = make()
+    import oracle
+    rp64 = g.row_ptr.astype(np.int64)
+    for _ in range(args.warmup):
+        oracle.labels_uf_csr(rp64, g.col)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.labels_uf_csr(rp64, g.col)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = g.n_edges / (ms / 1000)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"whole {name} graph per step (union-find oracle, 1 thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1612_01178_gb300 as ccl
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    name, make = WORKLOADS[args.workload]
+    t0 = time.perf_counter()
+    g = make()
+    gen_s = time.perf_counter() - t0
+
+    stream = torch.cuda.Stream(device=dev)
+    flags = ccl.CC_FLAG_SYMMETRIC
+    cc = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, segments=args.segments,
+                                 mode={"persistent": ccl.CC_MODE_PERSISTENT,
+                                       "multi": ccl.CC_MODE_MULTI_LAUNCH}[args.mode])
+    with torch.cuda.stream(stream):
+        rp = torch.from_numpy(g.row_ptr).to(dev, non_blocking=False)
+        col = torch.from_numpy(g.col).to(dev, non_blocking=False)
+        labels = torch.empty(g.n_vertices, dtype=torch.int32, device=dev)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream.synchronize()
+
+    # correctness of this exact launch configuration against the oracle (rank 0 also times it)
+    cc.csr(rp, col, labels)
+    cc.sync()
+    gpu_labels = labels.cpu().numpy()
+    info = cc.run_info()
+
+    cpu = None
+    parity = None
+    if rank == 0:
+        if world == 1:
+            rate, runs, ref = cpu_oracle_rate(g, budget_s=args.cpu_budget)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"whole {name} graph, {runs} run(s) of the union-find oracle on 1 host thread"}
+        else:
+            import oracle
+            ref, _ = oracle.labels_uf_csr(g.row_ptr.astype(np.int64), g.col)
+        parity = "bit-exact" if np.array_equal(ref, gpu_labels) else "MISMATCH"
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cc.csr(rp, col, labels)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        step()
+    cc.sync()
+    torch.cuda.synchronize()
+
+    gpu_id = str(local_rank)
+    try:
+        uuid = torch.cuda.get_device_properties(dev).uuid
+        gpu_id = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
+    except Exception:
+        pass
+    if "CUDA_VISIBLE_DEVICES" in os.environ and gpu_id == str(local_rank):
+        gpu_id = os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]
+    sampler = ClockSampler(gpu_id)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    events = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        events.append(step())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    cc.sync()  # raises if any timed launch reported a device error
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    ms = statistics.mean(step_ms)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    launches = info["launches"] * args.steps
+
+    # end to end through the host-buffer entry point (pinned host inputs, labels read back)
+    e2e = None
+    if not args.no_e2e:
+        pin_rp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+        pin_col = torch.from_numpy(g.col).pin_memory().numpy()
+        pin_out = torch.empty(g.n_vertices, dtype=torch.int32).pin_memory().numpy()
+        cc_host = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, segments=args.segments)
+        for _ in range(max(1, args.warmup)):
+            cc_host.csr_host(pin_rp, pin_col, pin_out)
+        n_e2e = max(3, min(args.steps, 20))
+        if dist is not None:
+            dist.barrier()
+        tt = []
+        for _ in range(n_e2e):
+            t1 = time.perf_counter()
+            cc_host.csr_host(pin_rp, pin_col, pin_out)
+            tt.append(time.perf_counter() - t1)
+        e2e_s = statistics.mean(tt)
+        if dist is not None:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_ok = np.array_equal(pin_out, gpu_labels)
+        cc_host.close()
+        e2e = {"value": world * g.n_edges / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
+               "d2h_bytes_per_step": int(4 * g.n_vertices), "ms_per_step": 1000 * e2e_s,
+               "labels_match": bool(e2e_ok)}
+
+    if rank != 0:
+        cc.close()
+        return 0
+    peak, peak_kind = measured_peaks()
+    b_alg = algorithmic_bytes(g)
+    achieved = b_alg / (ms / 1000) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": world * g.n_edges / (ms_max / 1000),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges,
+            "row_ptr": str(g.row_ptr.dtype), "seed": 1, "mode": args.mode, "segments": info["segments"],
+            "grid_blocks": info["grid_blocks"], "block": info["block"], "flags": "CC_FLAG_SYMMETRIC",
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "generation_s": round(gen_s, 3),
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "bytes_alg_per_launch": b_alg, "kernel": "k_csr_persistent",
+                     "kernel_ms_mean": ms, "kernel_ms_min": min(step_ms)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "parity": parity,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    cc.close()
+    return 0 if parity == "bit-exact" else 3
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="grid")
+    ap.add_argument("--mode", choices=["persistent", "multi"], default="persistent")
+    ap.add_argument("--segments", type=int, default=0, help="0 = the average degree (Section III-B)")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing for cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "ours":
+        args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+        try:
+            return run_ours(args, rank, world, local_rank)
+        finally:
+            dist.destroy_process_group()
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

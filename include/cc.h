@@ -1,0 +1,171 @@
+/*
+ * cc.h - C ABI of the GB300 (sm_103a) connected-components library (libcc.so).
+ *
+ * The library labels every vertex of an undirected graph G(V, E) with the index
+ * of a representative vertex of its connected component (Section II of Sutton,
+ * Ben-Nun, Barak, Pai, Pingali, "Adaptive Work-Efficient Connected Components
+ * on the GPU", arXiv:1612.01178). The representative is the MINIMUM vertex ID of
+ * the component: it falls out of the high-to-low hooking rule (Section II, Fig. 2
+ * and Section III-A, Fig. 3), which only ever points a tree root at a smaller
+ * vertex, so the root of every tree is its minimum vertex.
+ *
+ * Method (Section III, Fig. 4, "Adaptive Hook-Compress"):
+ *   pi(v) <- v for all v;
+ *   split the arcs into s = 2|E|/|V| segments (the average degree; Section III-B);
+ *   for each segment: Atomic-Hook every arc of the segment (Fig. 3, top: CAS a
+ *   root H = max to L = min, climbing until the CAS succeeds or both endpoints
+ *   share a tree), then Multi-Jump every vertex (Fig. 3, bottom: pointer-jump
+ *   until pi(v) is a root, writing every step).
+ * The whole loop runs on the device; no host round-trip decides convergence.
+ *
+ * Conventions shared by every entry point:
+ *   - Graph and label pointers are DEVICE pointers owned by the caller (except
+ *     cc_labels_csr_host, which takes host pointers). The library keeps no
+ *     reference to them after the call returns and never frees them.
+ *   - labels is int32[n_vertices], written in place: it is the parent array pi
+ *     of the method and holds the final labels when the work completes. No
+ *     other per-vertex memory is allocated. labels must not overlap the graph
+ *     arrays (checked on the host: CC_ERR_INVALID_ARG).
+ *   - Every arc/edge is read as an undirected edge. Self-loops and duplicate
+ *     edges are allowed. n_vertices = 0 and zero arcs are legal.
+ *   - Calls are asynchronous and ordered on the context's stream unless
+ *     CC_FLAG_SYNC is set. Argument errors are returned at once. Errors found
+ *     on the device (an endpoint outside [0, V), a wait that ran out, a failed
+ *     guard) are sticky in the context's device status word and are returned
+ *     by cc_sync (or by the call itself with CC_FLAG_SYNC), which also clears
+ *     them. While an error is pending, later device work of the same context
+ *     exits early. Device code never traps.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef CC_H_
+#define CC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc_ctx cc_ctx;
+
+typedef enum cc_status {
+  CC_OK = 0,
+  CC_ERR_INVALID_ARG = 1,  /* bad argument detected on the host (sizes, null pointers, types) */
+  CC_ERR_OUT_OF_RANGE = 2, /* device: an endpoint outside [0, V), or (CC_FLAG_VALIDATE) bad offsets */
+  CC_ERR_OOM = 3,          /* a context-owned allocation failed */
+  CC_ERR_CUDA = 4,         /* a CUDA runtime call failed; see cc_last_error_message */
+  CC_ERR_TIMEOUT = 5,      /* device: a grid-wide wait exceeded cc_options.timeout_ns */
+  CC_ERR_INTERNAL = 6      /* device: an iteration guard fired (impossible on valid input) */
+} cc_status;
+
+/* Row-offset element type of a CSR graph. */
+typedef enum cc_index_type { CC_INDEX_I32 = 4, CC_INDEX_I64 = 8 } cc_index_type;
+
+/* Flags (cc_options.flags, or'ed). */
+enum {
+  /* Every arc (u,v) has its reverse (v,u) (a symmetrised CSR): arcs with u >= v
+     are skipped, halving the hooks without changing any label. */
+  CC_FLAG_SYMMETRIC = 1,
+  /* Check offsets (row_ptr[0] = 0, non-decreasing, row_ptr[V] = n_arcs) and
+     endpoints on the device before hooking. Endpoints are always range-checked
+     while hooking; this adds the offset checks. */
+  CC_FLAG_VALIDATE = 2,
+  /* Block until the device work of the call is done and return its status. */
+  CC_FLAG_SYNC = 4
+};
+
+/* How the segment loop of Fig. 4 is driven on the device. */
+typedef enum cc_mode {
+  CC_MODE_AUTO = 0,        /* choose per graph size (currently: persistent) */
+  CC_MODE_PERSISTENT = 1,  /* one cooperative launch; phases separated by grid barriers */
+  CC_MODE_MULTI_LAUNCH = 2 /* Fig. 4 as printed: one init, then Hook and Multi-Jump kernels per segment */
+} cc_mode;
+
+typedef struct cc_options {
+  int32_t mode;        /* cc_mode */
+  int32_t segments;    /* s; 0 = max(1, round(n_arcs / n_vertices)) (Section III-B; n_arcs = 2|E|) */
+  int32_t block;       /* threads per block; 0 = 256 */
+  int32_t grid_blocks; /* blocks per launch; 0 = all co-resident blocks (occupancy x SMs) */
+  int32_t flags;       /* CC_FLAG_* */
+  int32_t reserved;    /* must be 0 */
+  int64_t timeout_ns;  /* limit of every device-side wait; 0 = 2 s */
+} cc_options;
+
+/* Fills *opt with the defaults (all zero fields resolved as documented above). */
+void cc_default_options(cc_options* opt);
+
+/* Creates a context on `device`. `stream` is a cudaStream_t to issue work on
+   (NULL = the legacy default stream). `opt` may be NULL (defaults). Allocates a
+   small device status block and a pinned host mirror of it. */
+cc_status cc_create(cc_ctx** out, int device, void* stream, const cc_options* opt);
+
+/* Replaces the stream / options of a context. */
+cc_status cc_set_stream(cc_ctx* ctx, void* stream);
+cc_status cc_set_options(cc_ctx* ctx, const cc_options* opt);
+
+/* Connected components of a CSR graph (Fig. 4 over the arcs of the CSR).
+ *   n_vertices  V >= 0.
+ *   n_arcs      number of stored arcs (= row_ptr[V]); for a symmetrised CSR, 2|E|.
+ *   row_ptr     device, int32 or int64 (row_ptr_type) [V + 1]; arcs of row u are
+ *               col_idx[row_ptr[u] .. row_ptr[u+1]).
+ *   col_idx     device int32 [n_arcs], values in [0, V).
+ *   labels      device int32 [V], caller-owned output (also the work array pi).
+ * The s segments are s contiguous, equal-length ranges of the arc array
+ * (Fig. 4: "s distinct subsets of E"). */
+cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                        cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels);
+
+/* Connected components of an edge list (COO): edge i joins src[i] and dst[i].
+ *   src, dst    device int32 [n_edges], values in [0, V); each edge is undirected
+ *               and is hooked once.
+ *   labels      device int32 [V], caller-owned output.
+ * s defaults to max(1, round(2 n_edges / V)). */
+cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const int32_t* src,
+                        const int32_t* dst, int32_t* labels);
+
+/* cc_labels_csr with HOST buffers: copies row_ptr and col_idx from host memory
+   (pinned memory gives full copy bandwidth) into context-owned device buffers,
+   runs the method, copies the labels back into the host array `labels`, and
+   returns after the copy completes (always synchronous). The device buffers
+   grow to the largest graph seen and are freed by cc_destroy. */
+cc_status cc_labels_csr_host(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                             cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels);
+
+/* Waits for all work issued on the context's stream, then returns the first
+   device error recorded since the last cc_sync (CC_OK if none) and clears it. */
+cc_status cc_sync(cc_ctx* ctx);
+
+/* What the last labelling call ran with (filled on the host at issue time). */
+typedef struct cc_run_info {
+  int32_t mode;        /* cc_mode actually used */
+  int32_t segments;    /* s actually used */
+  int32_t grid_blocks; /* blocks per launch */
+  int32_t block;       /* threads per block */
+  int32_t launches;    /* kernel launches issued by the call */
+  int32_t reserved;
+} cc_run_info;
+cc_status cc_last_run_info(const cc_ctx* ctx, cc_run_info* info);
+
+/* Text of the last CUDA error seen by the context ("" if none). */
+const char* cc_last_error_message(const cc_ctx* ctx);
+
+/* Static description of a status code. */
+const char* cc_status_string(cc_status status);
+
+/* Releases the context and everything it allocated. NULL is ignored. Waits for
+   the context's stream first. */
+void cc_destroy(cc_ctx* ctx);
+
+/* Test hook: with block >= 0, that block of the next persistent launch does not
+   arrive at its first grid barrier, so every other block's wait runs out after
+   timeout_ns and the call reports CC_ERR_TIMEOUT; the context stays usable.
+   The hook disarms itself after one launch. Returns CC_ERR_INVALID_ARG for a
+   NULL context. */
+cc_status cc_debug_skip_barrier_arrival(cc_ctx* ctx, int32_t block);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H_ */

@@ -1,0 +1,322 @@
+"""Python binding of libcc.so (include/cc.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module only turns
+torch CUDA tensors into device pointers and sizes. There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+The function names follow the C ABI: ``cc_create``, ``cc_labels_csr``,
+``cc_labels_coo``, ``cc_labels_csr_host``, ``cc_labels_batched``, ``cc_sync``,
+``cc_destroy``. ``ConnectedComponents`` wraps a context for convenient use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# status codes (cc_status)
+CC_OK = 0
+CC_ERR_INVALID_ARG = 1
+CC_ERR_OUT_OF_RANGE = 2
+CC_ERR_OOM = 3
+CC_ERR_CUDA = 4
+CC_ERR_TIMEOUT = 5
+CC_ERR_INTERNAL = 6
+
+# flags
+CC_FLAG_SYMMETRIC = 1
+CC_FLAG_VALIDATE = 2
+CC_FLAG_SYNC = 4
+
+# modes
+CC_MODE_AUTO = 0
+CC_MODE_PERSISTENT = 1
+CC_MODE_MULTI_LAUNCH = 2
+
+CC_INDEX_I32 = 4
+CC_INDEX_I64 = 8
+
+
+class cc_options(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("segments", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("timeout_ns", ctypes.c_int64),
+    ]
+
+
+class cc_run_info(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("segments", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {status_string(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# Every exported symbol with its ctypes signature (restype, argtypes).
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "cc_default_options": (None, [ctypes.POINTER(cc_options)]),
+    "cc_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(cc_options)]),
+    "cc_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "cc_set_options": (ctypes.c_int, [_vp, ctypes.POINTER(cc_options)]),
+    "cc_labels_csr": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
+    "cc_labels_coo": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
+    "cc_labels_csr_host": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
+    "cc_sync": (ctypes.c_int, [_vp]),
+    "cc_last_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(cc_run_info)]),
+    "cc_last_error_message": (ctypes.c_char_p, [_vp]),
+    "cc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cc_destroy": (None, [_vp]),
+    "cc_debug_skip_barrier_arrival": (ctypes.c_int, [_vp, _i32]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libcc.so (building it first if it is missing or stale and nvcc is present)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            path = _build.LIB_PATH
+            if build_if_missing and (not os.path.exists(path) or _build.is_stale()):
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libcc.so not found at {path}; run paper_1612_01178_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().cc_status_string(int(status)).decode()
+    except Exception:  # the library itself failed to load
+        return f"status {status}"
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != CC_OK:
+        detail = ""
+        if ctx is not None:
+            detail = load().cc_last_error_message(ctx).decode()
+        raise CCError(status, where, detail)
+
+
+def default_options(**kw) -> cc_options:
+    o = cc_options()
+    load().cc_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def cc_create(device: int = 0, stream=None, options: cc_options | None = None):
+    """Create a context on `device` issuing work on `stream` (a torch.cuda.Stream or handle)."""
+    lib = load()
+    h = ctypes.c_void_p()
+    opt = options if options is not None else default_options()
+    st = lib.cc_create(ctypes.byref(h), int(device), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(opt))
+    _check(st, "cc_create")
+    return h
+
+
+def cc_destroy(ctx) -> None:
+    if ctx:
+        load().cc_destroy(ctx)
+
+
+def cc_set_options(ctx, options: cc_options) -> None:
+    _check(load().cc_set_options(ctx, ctypes.byref(options)), "cc_set_options", ctx)
+
+
+def cc_set_stream(ctx, stream) -> None:
+    _check(load().cc_set_stream(ctx, ctypes.c_void_p(_stream_handle(stream))), "cc_set_stream", ctx)
+
+
+def cc_sync(ctx) -> int:
+    """Wait for the context's stream; raise on a pending device error."""
+    st = load().cc_sync(ctx)
+    _check(st, "cc_sync", ctx)
+    return st
+
+
+def cc_last_run_info(ctx) -> dict:
+    info = cc_run_info()
+    _check(load().cc_last_run_info(ctx, ctypes.byref(info)), "cc_last_run_info")
+    return {k: getattr(info, k) for k, _ in cc_run_info._fields_ if k != "reserved"}
+
+
+def _dev_tensor(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def cc_labels_csr(ctx, row_ptr, col_idx, labels=None):
+    """Min-ID component labels of a CSR graph held in CUDA tensors (int32/int64 row_ptr, int32 col_idx).
+
+    Returns the int32 labels tensor (allocated with torch if not given). Asynchronous on the
+    context's stream unless the context has CC_FLAG_SYNC."""
+    import torch
+    if row_ptr.dtype not in (torch.int32, torch.int64):
+        raise TypeError("row_ptr must be int32 or int64")
+    _dev_tensor(row_ptr, row_ptr.dtype, "row_ptr")
+    _dev_tensor(col_idx, torch.int32, "col_idx")
+    V = row_ptr.numel() - 1
+    if V < 0:
+        raise ValueError("row_ptr must hold V+1 offsets")
+    if labels is None:
+        labels = torch.empty(V, dtype=torch.int32, device=row_ptr.device)
+    _dev_tensor(labels, torch.int32, "labels")
+    if labels.numel() != V:
+        raise ValueError("labels must hold V entries")
+    itype = CC_INDEX_I64 if row_ptr.dtype == torch.int64 else CC_INDEX_I32
+    st = load().cc_labels_csr(ctx, V, col_idx.numel(), row_ptr.data_ptr(), itype,
+                              col_idx.data_ptr() if col_idx.numel() else None,
+                              labels.data_ptr() if V else None)
+    _check(st, "cc_labels_csr", ctx)
+    return labels
+
+
+def cc_labels_coo(ctx, n_vertices: int, src, dst, labels=None):
+    """Min-ID component labels of an undirected edge list (int32 CUDA tensors src, dst)."""
+    import torch
+    _dev_tensor(src, torch.int32, "src")
+    _dev_tensor(dst, torch.int32, "dst")
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    if labels is None:
+        labels = torch.empty(n_vertices, dtype=torch.int32, device=src.device)
+    _dev_tensor(labels, torch.int32, "labels")
+    if labels.numel() != n_vertices:
+        raise ValueError("labels must hold n_vertices entries")
+    st = load().cc_labels_coo(ctx, int(n_vertices), src.numel(), src.data_ptr() if src.numel() else None,
+                              dst.data_ptr() if dst.numel() else None, labels.data_ptr() if n_vertices else None)
+    _check(st, "cc_labels_coo", ctx)
+    return labels
+
+
+def cc_labels_csr_host(ctx, row_ptr: np.ndarray, col_idx: np.ndarray, labels: np.ndarray | None = None):
+    """cc_labels_csr on host (numpy) arrays; synchronous. Pinned arrays copy fastest."""
+    rp = row_ptr
+    if rp.dtype not in (np.int32, np.int64) or not rp.flags.c_contiguous:
+        raise TypeError("row_ptr must be a contiguous int32/int64 array")
+    if col_idx.dtype != np.int32 or not col_idx.flags.c_contiguous:
+        raise TypeError("col_idx must be a contiguous int32 array")
+    V = rp.shape[0] - 1
+    if labels is None:
+        labels = np.empty(V, np.int32)
+    if labels.dtype != np.int32 or labels.shape[0] != V or not labels.flags.c_contiguous:
+        raise TypeError("labels must be a contiguous int32 array of V entries")
+    itype = CC_INDEX_I64 if rp.dtype == np.int64 else CC_INDEX_I32
+    st = load().cc_labels_csr_host(ctx, V, col_idx.shape[0], rp.ctypes.data, itype,
+                                   col_idx.ctypes.data if col_idx.size else None,
+                                   labels.ctypes.data if V else None)
+    _check(st, "cc_labels_csr_host", ctx)
+    return labels
+
+
+def cc_debug_skip_barrier_arrival(ctx, block: int) -> None:
+    _check(load().cc_debug_skip_barrier_arrival(ctx, int(block)), "cc_debug_skip_barrier_arrival")
+
+
+class ConnectedComponents:
+    """A library context bound to one device and stream.
+
+    >>> cc = ConnectedComponents(flags=CC_FLAG_SYMMETRIC)
+    >>> labels = cc.csr(row_ptr, col_idx); cc.sync()
+    """
+
+    def __init__(self, device: int = 0, stream=None, **options):
+        self.device = device
+        self.options = default_options(**options)
+        self._ctx = cc_create(device, stream, self.options)
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            setattr(self.options, k, int(v))
+        cc_set_options(self._ctx, self.options)
+
+    def set_stream(self, stream):
+        cc_set_stream(self._ctx, stream)
+
+    def csr(self, row_ptr, col_idx, labels=None):
+        return cc_labels_csr(self._ctx, row_ptr, col_idx, labels)
+
+    def coo(self, n_vertices, src, dst, labels=None):
+        return cc_labels_coo(self._ctx, n_vertices, src, dst, labels)
+
+    def csr_host(self, row_ptr, col_idx, labels=None):
+        return cc_labels_csr_host(self._ctx, row_ptr, col_idx, labels)
+
+    def sync(self):
+        return cc_sync(self._ctx)
+
+    def run_info(self):
+        return cc_last_run_info(self._ctx)
+
+    def close(self):
+        if self._ctx:
+            cc_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

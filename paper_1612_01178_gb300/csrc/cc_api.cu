@@ -1,0 +1,386 @@
+// C ABI of libcc.so (declared in include/cc.h): contexts, argument checks, launch-shape
+// choice, device status handling and the host-buffer entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "cc.h"
+#include "cc_internal.h"
+
+struct cc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cc_options opt{};
+  int num_sms = 0;
+  cc::DevStatus* d_status = nullptr;  // device status block
+  cc::DevStatus* h_status = nullptr;  // pinned host mirror
+  cc_run_info last{};
+  int skip_arrival_block = -1;
+  char last_error[256] = {0};
+  // staging buffers of cc_labels_csr_host
+  void* d_rp = nullptr;
+  size_t d_rp_bytes = 0;
+  int32_t* d_col = nullptr;
+  size_t d_col_bytes = 0;
+  int32_t* d_labels = nullptr;
+  size_t d_labels_bytes = 0;
+};
+
+namespace {
+
+constexpr long long kDefaultTimeoutNs = 2000000000LL;
+
+// Makes `device` current for the scope of a call and restores the caller's device after.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = (prev == device) || cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cc_status cuda_fail(cc_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) std::snprintf(ctx->last_error, sizeof(ctx->last_error), "%s: %s", where, cudaGetErrorString(e));
+  cudaGetLastError();  // clear a non-sticky error so the context stays usable
+  return CC_ERR_CUDA;
+}
+
+void resolve_options(cc_options* o) {
+  if (o->block <= 0) o->block = 256;
+  if (o->timeout_ns <= 0) o->timeout_ns = kDefaultTimeoutNs;
+}
+
+bool options_ok(const cc_options* o) {
+  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_MULTI_LAUNCH) return false;
+  if (o->segments < 0 || o->grid_blocks < 0 || o->reserved != 0) return false;
+  if (o->block != 0 && (o->block < 32 || o->block > 256 || o->block % 32 != 0)) return false;
+  if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC)) return false;
+  return true;
+}
+
+// s of Section III-B: 2|E|/|V| = arcs per vertex, rounded, at least 1.
+int default_segments(long long arcs, long long V) {
+  if (V <= 0 || arcs <= 0) return 1;
+  const double s = std::floor((double)arcs / (double)V + 0.5);
+  return (int)std::max(1.0, std::min(s, 1.0e6));
+}
+
+cc_status read_and_clear_status(cc_ctx* ctx) {
+  cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(cc::DevStatus), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_sync");
+  const int err = ctx->h_status->error;
+  if (err != 0) {
+    std::snprintf(ctx->last_error, sizeof(ctx->last_error), "device error %d at site %d (info %lld)", err,
+                  ctx->h_status->error_where, ctx->h_status->error_info);
+    e = cudaMemsetAsync(ctx->d_status, 0, sizeof(cc::DevStatus), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_sync clear");
+    return (cc_status)err;
+  }
+  return CC_OK;
+}
+
+// Runs one single-graph problem on the context's stream.
+cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
+  const cc_options& o = ctx->opt;
+  const int block = o.block;
+  p.segments = o.segments > 0 ? o.segments : default_segments(p.m, p.V);
+  if (p.m == 0) p.segments = 1;
+
+  cc::Ctl c;
+  c.st = ctx->d_status;
+  c.timeout_ns = o.timeout_ns;
+  c.skip_arrival_block = -1;
+
+  // Work-proportional grid, capped by what is co-resident (the persistent kernel needs it).
+  const long long work = std::max<long long>(p.V, p.m / 4);
+  long long want = (work + block - 1) / block;
+  want = std::max<long long>(want, 1);
+
+  cc_run_info info{};
+  info.block = block;
+  info.segments = p.segments;
+  int mode = o.mode == CC_MODE_AUTO ? CC_MODE_PERSISTENT : o.mode;
+  info.mode = mode;
+
+  if (o.flags & CC_FLAG_VALIDATE) {
+    cc::LaunchShape vs{(int)std::min<long long>(want, (long long)ctx->num_sms * 8), block};
+    cudaError_t e = cc::launch_validate(p, c, vs, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate launch");
+    info.launches += 1;
+  }
+
+  if (mode == CC_MODE_PERSISTENT) {
+    const int per_sm = cc::persistent_blocks_per_sm(p, block);
+    if (per_sm <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "persistent occupancy");
+    const long long cap = (long long)per_sm * ctx->num_sms;
+    long long grid = o.grid_blocks > 0 ? std::min<long long>(o.grid_blocks, cap) : std::min(want, cap);
+    cc::LaunchShape s{(int)grid, block};
+    c.skip_arrival_block = ctx->skip_arrival_block;
+    ctx->skip_arrival_block = -1;
+    cudaError_t e = cudaMemsetAsync(&ctx->d_status->bar, 0, sizeof(unsigned int), ctx->stream);
+    if (e == cudaSuccess) e = cc::launch_persistent(p, c, s, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
+    info.grid_blocks = s.grid;
+    info.launches += 1;
+  } else {
+    const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
+    const long long cap = (long long)per_sm * ctx->num_sms;
+    long long grid = o.grid_blocks > 0 ? o.grid_blocks : std::min(want, cap);
+    cc::LaunchShape s{(int)grid, block};
+    int n = 0;
+    cudaError_t e = cc::launch_multi(p, c, s, ctx->stream, &n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "multi launch");
+    info.grid_blocks = s.grid;
+    info.launches += n;
+  }
+  ctx->last = info;
+  if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_default_options(cc_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->mode = CC_MODE_AUTO;
+  opt->block = 256;
+  opt->timeout_ns = kDefaultTimeoutNs;
+}
+
+cc_status cc_create(cc_ctx** out, int device, void* stream, const cc_options* opt) {
+  if (!out) return CC_ERR_INVALID_ARG;
+  *out = nullptr;
+  cc_options o;
+  cc_default_options(&o);
+  if (opt) {
+    if (!options_ok(opt)) return CC_ERR_INVALID_ARG;
+    o = *opt;
+  }
+  resolve_options(&o);
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return device < 0 ? CC_ERR_INVALID_ARG : CC_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok) return CC_ERR_CUDA;
+  cc_ctx* ctx = new (std::nothrow) cc_ctx();
+  if (!ctx) return CC_ERR_OOM;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->opt = o;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    cudaGetLastError();
+    return CC_ERR_CUDA;
+  }
+  if (cudaMalloc(&ctx->d_status, sizeof(cc::DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(cc::DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return CC_ERR_OOM;
+  }
+  std::memset(ctx->h_status, 0, sizeof(cc::DevStatus));
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, sizeof(cc::DevStatus), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return CC_ERR_CUDA;
+  }
+  *out = ctx;
+  return CC_OK;
+}
+
+cc_status cc_set_stream(cc_ctx* ctx, void* stream) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return CC_OK;
+}
+
+cc_status cc_set_options(cc_ctx* ctx, const cc_options* opt) {
+  if (!ctx || !opt || !options_ok(opt)) return CC_ERR_INVALID_ARG;
+  ctx->opt = *opt;
+  resolve_options(&ctx->opt);
+  return CC_OK;
+}
+
+static bool overlaps(const void* a, size_t a_bytes, const void* b, size_t b_bytes) {
+  if (!a || !b || a_bytes == 0 || b_bytes == 0) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + b_bytes && y < x + a_bytes;
+}
+
+cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                        cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_vertices < 0 || n_vertices > INT32_MAX || n_arcs < 0) return CC_ERR_INVALID_ARG;
+  if (row_ptr_type != CC_INDEX_I32 && row_ptr_type != CC_INDEX_I64) return CC_ERR_INVALID_ARG;
+  if (row_ptr_type == CC_INDEX_I32 && n_arcs > INT32_MAX) return CC_ERR_INVALID_ARG;
+  if (!row_ptr) return CC_ERR_INVALID_ARG;
+  if (n_vertices > 0 && !labels) return CC_ERR_INVALID_ARG;
+  if (n_arcs > 0 && (!col_idx || n_vertices == 0)) return CC_ERR_INVALID_ARG;
+  const size_t lab_bytes = (size_t)n_vertices * 4;
+  if (overlaps(labels, lab_bytes, row_ptr, (size_t)(n_vertices + 1) * (size_t)row_ptr_type) ||
+      overlaps(labels, lab_bytes, col_idx, (size_t)n_arcs * 4))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  if (n_vertices == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  cc::Problem p{};
+  p.kind = cc::kKindCsr;
+  p.rp = row_ptr;
+  p.rp64 = row_ptr_type == CC_INDEX_I64;
+  p.col = col_idx;
+  p.pi = labels;
+  p.V = (int)n_vertices;
+  p.m = n_arcs;
+  p.sym = (ctx->opt.flags & CC_FLAG_SYMMETRIC) != 0;
+  return run_problem(ctx, p);
+}
+
+cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const int32_t* src, const int32_t* dst,
+                        int32_t* labels) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_vertices < 0 || n_vertices > INT32_MAX || n_edges < 0) return CC_ERR_INVALID_ARG;
+  if (n_vertices > 0 && !labels) return CC_ERR_INVALID_ARG;
+  if (n_edges > 0 && (!src || !dst || n_vertices == 0)) return CC_ERR_INVALID_ARG;
+  if (overlaps(labels, (size_t)n_vertices * 4, src, (size_t)n_edges * 4) ||
+      overlaps(labels, (size_t)n_vertices * 4, dst, (size_t)n_edges * 4))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  if (n_vertices == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  cc::Problem p{};
+  p.kind = cc::kKindCoo;
+  p.src = src;
+  p.dst = dst;
+  p.pi = labels;
+  p.V = (int)n_vertices;
+  p.m = n_edges;
+  p.sym = false;
+  cc_options saved = ctx->opt;
+  // Section III-B: s = 2|E| / |V| with |E| edges.
+  if (ctx->opt.segments == 0) ctx->opt.segments = default_segments(2 * n_edges, n_vertices);
+  cc_status st = run_problem(ctx, p);
+  ctx->opt = saved;
+  return st;
+}
+
+static cc_status grow(cc_ctx* ctx, void** buf, size_t* have, size_t need) {
+  if (need <= *have) return CC_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    std::snprintf(ctx->last_error, sizeof(ctx->last_error), "staging allocation of %zu bytes failed", need);
+    return CC_ERR_OOM;
+  }
+  *have = need;
+  return CC_OK;
+}
+
+cc_status cc_labels_csr_host(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                             cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_vertices < 0 || n_vertices > INT32_MAX || n_arcs < 0 || !row_ptr) return CC_ERR_INVALID_ARG;
+  if (row_ptr_type != CC_INDEX_I32 && row_ptr_type != CC_INDEX_I64) return CC_ERR_INVALID_ARG;
+  if (n_vertices > 0 && !labels) return CC_ERR_INVALID_ARG;
+  if (n_arcs > 0 && !col_idx) return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  const size_t rp_bytes = (size_t)(n_vertices + 1) * (size_t)row_ptr_type;
+  const size_t col_bytes = (size_t)n_arcs * sizeof(int32_t);
+  const size_t lab_bytes = (size_t)n_vertices * sizeof(int32_t);
+  cc_status st = grow(ctx, &ctx->d_rp, &ctx->d_rp_bytes, std::max<size_t>(rp_bytes, 16));
+  if (st == CC_OK) st = grow(ctx, (void**)&ctx->d_col, &ctx->d_col_bytes, std::max<size_t>(col_bytes, 16));
+  if (st == CC_OK) st = grow(ctx, (void**)&ctx->d_labels, &ctx->d_labels_bytes, std::max<size_t>(lab_bytes, 16));
+  if (st != CC_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(ctx->d_rp, row_ptr, rp_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && col_bytes)
+    e = cudaMemcpyAsync(ctx->d_col, col_idx, col_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+  const int saved_flags = ctx->opt.flags;
+  ctx->opt.flags &= ~CC_FLAG_SYNC;
+  st = cc_labels_csr(ctx, n_vertices, n_arcs, ctx->d_rp, row_ptr_type, ctx->d_col, ctx->d_labels);
+  ctx->opt.flags = saved_flags;
+  if (st != CC_OK) return st;
+  if (lab_bytes) {
+    e = cudaMemcpyAsync(labels, ctx->d_labels, lab_bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
+  }
+  return read_and_clear_status(ctx);
+}
+
+cc_status cc_sync(cc_ctx* ctx) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  return read_and_clear_status(ctx);
+}
+
+cc_status cc_last_run_info(const cc_ctx* ctx, cc_run_info* info) {
+  if (!ctx || !info) return CC_ERR_INVALID_ARG;
+  *info = ctx->last;
+  return CC_OK;
+}
+
+const char* cc_last_error_message(const cc_ctx* ctx) { return ctx ? ctx->last_error : ""; }
+
+const char* cc_status_string(cc_status s) {
+  switch (s) {
+    case CC_OK: return "CC_OK";
+    case CC_ERR_INVALID_ARG: return "CC_ERR_INVALID_ARG: invalid argument";
+    case CC_ERR_OUT_OF_RANGE: return "CC_ERR_OUT_OF_RANGE: endpoint outside [0, V) or malformed offsets";
+    case CC_ERR_OOM: return "CC_ERR_OOM: allocation failed";
+    case CC_ERR_CUDA: return "CC_ERR_CUDA: CUDA runtime error";
+    case CC_ERR_TIMEOUT: return "CC_ERR_TIMEOUT: a device-side wait exceeded its limit";
+    case CC_ERR_INTERNAL: return "CC_ERR_INTERNAL: device iteration guard fired";
+  }
+  return "unknown cc_status";
+}
+
+void cc_destroy(cc_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_rp) cudaFree(ctx->d_rp);
+    if (ctx->d_col) cudaFree(ctx->d_col);
+    if (ctx->d_labels) cudaFree(ctx->d_labels);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    cudaGetLastError();
+  }
+  delete ctx;
+}
+
+cc_status cc_debug_skip_barrier_arrival(cc_ctx* ctx, int32_t block) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->skip_arrival_block = block;
+  return CC_OK;
+}
+
+}  // extern "C"

@@ -157,6 +157,32 @@ const char* cc_status_string(cc_status status);
    the context's stream first. */
 void cc_destroy(cc_ctx* ctx);
 
+/* Allocation-free variant of cc_labels_csr (the paper has no counterpart: this
+   entry point exists for callers that cannot allocate device memory, such as code
+   running inside a device memory allocator or pool, plug-ins whose host owns all
+   device memory, or real-time paths that must not allocate).
+   It needs no context and calls no cudaMalloc/cudaFree or allocating routine. The
+   only scratch the persistent kernel needs beyond the caller's arrays (a 64-byte
+   grid-barrier counter and error word) lives in a static 256-byte device array
+   inside libcc.so, held on every GPU that loads the library until the process
+   exits; its size does not grow with the graph. The graph limits are those of
+   cc_labels_csr: n_vertices <= 2^31 - 1, and n_arcs <= 2^31 - 1 with int32
+   offsets; anything larger, or any other flag than CC_FLAG_SYMMETRIC, returns
+   CC_ERR_INVALID_ARG.
+     row_ptr, col_idx, labels: device pointers as for cc_labels_csr, on the
+       current device; stream: cudaStream_t (NULL = legacy default stream).
+   The call issues on `stream`, waits for it, and returns the device status of
+   this call (CC_OK, CC_ERR_OUT_OF_RANGE, CC_ERR_TIMEOUT, ...). The first call on
+   a device looks up the scratch array's device address (cudaGetSymbolAddress,
+   once per device) and must therefore come before any stream capture on that
+   device. All calls share the scratch array, which keeps the last call's
+   contents; each call clears it before launching. Calls whose GPU work could
+   overlap (unordered streams, or concurrent host threads) race on it and must
+   not be issued. */
+cc_status cc_labels_csr_noalloc(int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                                cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels,
+                                void* stream, int32_t flags);
+
 /* Test hook: with block >= 0, that block of the next persistent launch does not
    arrive at its first grid barrier, so every other block's wait runs out after
    timeout_ns and the call reports CC_ERR_TIMEOUT; the context stays usable.

@@ -92,6 +92,7 @@ SIGNATURES = {
     "cc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cc_destroy": (None, [_vp]),
     "cc_debug_skip_barrier_arrival": (ctypes.c_int, [_vp, _i32]),
+    "cc_labels_csr_noalloc": (ctypes.c_int, [_i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _i32]),
 }
 
 
@@ -258,6 +259,31 @@ def cc_labels_csr_host(ctx, row_ptr: np.ndarray, col_idx: np.ndarray, labels: np
                                    col_idx.ctypes.data if col_idx.size else None,
                                    labels.ctypes.data if V else None)
     _check(st, "cc_labels_csr_host", ctx)
+    return labels
+
+
+def cc_labels_csr_noalloc(row_ptr, col_idx, labels, stream=None, symmetric: bool = False):
+    """Allocation-free labelling for callers that cannot allocate device memory.
+
+    Calls the C entry point of the same name, which uses a static scratch block inside
+    the library instead of a context; `labels` must be a preallocated int32 CUDA tensor
+    of V entries (this wrapper allocates nothing). Synchronous on `stream`."""
+    import torch
+    if row_ptr.dtype not in (torch.int32, torch.int64):
+        raise TypeError("row_ptr must be int32 or int64")
+    _dev_tensor(row_ptr, row_ptr.dtype, "row_ptr")
+    _dev_tensor(col_idx, torch.int32, "col_idx")
+    _dev_tensor(labels, torch.int32, "labels")
+    V = row_ptr.numel() - 1
+    if labels.numel() != V:
+        raise ValueError("labels must hold V entries")
+    itype = CC_INDEX_I64 if row_ptr.dtype == torch.int64 else CC_INDEX_I32
+    st = load().cc_labels_csr_noalloc(V, col_idx.numel(), row_ptr.data_ptr(), itype,
+                                      col_idx.data_ptr() if col_idx.numel() else None,
+                                      labels.data_ptr() if V else None,
+                                      ctypes.c_void_p(_stream_handle(stream)),
+                                      CC_FLAG_SYMMETRIC if symmetric else 0)
+    _check(st, "cc_labels_csr_noalloc")
     return labels
 
 

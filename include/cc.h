@@ -72,7 +72,10 @@ enum {
      while hooking; this adds the offset checks. */
   CC_FLAG_VALIDATE = 2,
   /* Block until the device work of the call is done and return its status. */
-  CC_FLAG_SYNC = 4
+  CC_FLAG_SYNC = 4,
+  /* Record a device timestamp at every grid barrier of a persistent launch
+     (read with cc_last_phase_times). Costs one store per barrier. */
+  CC_FLAG_PHASE_TIMES = 8
 };
 
 /* How the segment loop of Fig. 4 is driven on the device. */
@@ -85,9 +88,24 @@ typedef enum cc_mode {
 typedef struct cc_options {
   int32_t mode;        /* cc_mode */
   int32_t segments;    /* s; 0 = max(1, round(n_arcs / n_vertices)) (Section III-B; n_arcs = 2|E|) */
-  int32_t block;       /* threads per block; 0 = 256 */
+  int32_t block;       /* threads per block (a multiple of 32, at most 1024); 0 = 256 for the
+                          plain hook and 1024 for the two-phase hook. A block that cannot be
+                          co-resident is halved until it can. */
   int32_t grid_blocks; /* blocks per launch; 0 = all co-resident blocks (occupancy x SMs) */
   int32_t flags;       /* CC_FLAG_* */
+  int32_t chunk_arcs;  /* global Atomic-Hook work split: -1 or 0 = one fixed slice of the segment per
+                          warp; > 0 (a multiple of 32) = warps take chunks of this many arcs from a
+                          shared counter */
+  int32_t tile_vertices; /* window of the two-phase hierarchical Atomic-Hook (CSR, persistent mode):
+                          a power of two, 256 .. 32768. Phase A hooks every arc whose two ends lie
+                          in the same window of this many consecutive IDs in shared memory and
+                          writes those stars to pi; the other arcs form a worklist E' that phase B
+                          hooks on pi in s' = 2|E'|/|V| segments (or `segments` if set), each
+                          followed by a Multi-Jump. -1 = off: every arc is hooked on pi (Fig. 4
+                          as printed). 0 = automatic: graphs of at least 2^17 vertices whose
+                          sampled arcs mostly stay inside 32768-vertex windows use the two-phase
+                          hook; the sample is a small kernel plus a synchronisation on the first
+                          call for a given (row_ptr, col_idx, V, n_arcs), reused afterwards. */
   int32_t reserved;    /* must be 0 */
   int64_t timeout_ns;  /* limit of every device-side wait; 0 = 2 s */
 } cc_options;
@@ -143,9 +161,23 @@ typedef struct cc_run_info {
   int32_t grid_blocks; /* blocks per launch */
   int32_t block;       /* threads per block */
   int32_t launches;    /* kernel launches issued by the call */
-  int32_t reserved;
+  int32_t tile_vertices; /* window of the hierarchical hook (0 = plain hook) */
+  int64_t worklist_capacity; /* pairs the worklist could hold (hierarchical hook) */
 } cc_run_info;
+
+/* Worklist of the last hierarchical-hook launch: waits for the context's stream, then
+   stores the number of arcs phase A left for phase B (*pairs) and the segments phase B
+   used (*segments); both 0 if every arc was joined inside its window. */
+cc_status cc_last_worklist(cc_ctx* ctx, int64_t* pairs, int32_t* segments);
 cc_status cc_last_run_info(const cc_ctx* ctx, cc_run_info* info);
+
+/* Phase timestamps of the last persistent launch made with CC_FLAG_PHASE_TIMES:
+   waits for the context's stream, then writes ns[0] = 0 (kernel start),
+   ns[k] = time block 0 left grid barrier k (k = 1 .. n-2) and ns[n-1] = the
+   end of the last block, all in ns relative to the start; *n = entries written
+   (at most cap, at most 64). Barrier 1 ends init; barriers 2i and 2i+1 end the
+   Atomic-Hook and the Multi-Jump of segment i. */
+cc_status cc_last_phase_times(cc_ctx* ctx, int64_t* ns, int32_t cap, int32_t* n);
 
 /* Text of the last CUDA error seen by the context ("" if none). */
 const char* cc_last_error_message(const cc_ctx* ctx);

@@ -31,6 +31,7 @@ CC_ERR_INTERNAL = 6
 CC_FLAG_SYMMETRIC = 1
 CC_FLAG_VALIDATE = 2
 CC_FLAG_SYNC = 4
+CC_FLAG_PHASE_TIMES = 8
 
 # modes
 CC_MODE_AUTO = 0
@@ -48,6 +49,8 @@ class cc_options(ctypes.Structure):
         ("block", ctypes.c_int32),
         ("grid_blocks", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("chunk_arcs", ctypes.c_int32),
+        ("tile_vertices", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("timeout_ns", ctypes.c_int64),
     ]
@@ -60,7 +63,8 @@ class cc_run_info(ctypes.Structure):
         ("grid_blocks", ctypes.c_int32),
         ("block", ctypes.c_int32),
         ("launches", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_vertices", ctypes.c_int32),
+        ("worklist_capacity", ctypes.c_int64),
     ]
 
 
@@ -93,6 +97,8 @@ SIGNATURES = {
     "cc_destroy": (None, [_vp]),
     "cc_debug_skip_barrier_arrival": (ctypes.c_int, [_vp, _i32]),
     "cc_labels_csr_noalloc": (ctypes.c_int, [_i64, _i64, _vp, ctypes.c_int, _vp, _vp, _vp, _i32]),
+    "cc_last_phase_times": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _i32, ctypes.POINTER(_i32)]),
+    "cc_last_worklist": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
 }
 
 
@@ -184,7 +190,22 @@ def cc_sync(ctx) -> int:
 def cc_last_run_info(ctx) -> dict:
     info = cc_run_info()
     _check(load().cc_last_run_info(ctx, ctypes.byref(info)), "cc_last_run_info")
-    return {k: getattr(info, k) for k, _ in cc_run_info._fields_ if k != "reserved"}
+    return {k: getattr(info, k) for k, _ in cc_run_info._fields_}
+
+
+def cc_last_phase_times(ctx) -> list:
+    """Relative device timestamps (ns) of the last persistent launch made with CC_FLAG_PHASE_TIMES."""
+    buf = (_i64 * 64)()
+    n = _i32()
+    _check(load().cc_last_phase_times(ctx, buf, 64, ctypes.byref(n)), "cc_last_phase_times", ctx)
+    return [int(buf[i]) for i in range(n.value)]
+
+
+def cc_last_worklist(ctx) -> tuple:
+    """(pairs left for the global phase, segments it used) of the last hierarchical-hook launch."""
+    pairs, segs = _i64(), _i32()
+    _check(load().cc_last_worklist(ctx, ctypes.byref(pairs), ctypes.byref(segs)), "cc_last_worklist", ctx)
+    return pairs.value, segs.value
 
 
 def _dev_tensor(t, dtype, name):
@@ -329,6 +350,12 @@ class ConnectedComponents:
 
     def run_info(self):
         return cc_last_run_info(self._ctx)
+
+    def phase_times(self):
+        return cc_last_phase_times(self._ctx)
+
+    def worklist(self):
+        return cc_last_worklist(self._ctx)
 
     def close(self):
         if self._ctx:

@@ -21,6 +21,20 @@ struct cc_ctx {
   cc_run_info last{};
   int skip_arrival_block = -1;
   char last_error[256] = {0};
+  unsigned long long* d_phase = nullptr;  // CC_FLAG_PHASE_TIMES timestamps (kPhaseSlots)
+  bool phase_valid = false;
+  // worklist of the two-phase hierarchical hook
+  int2* d_wl = nullptr;
+  size_t d_wl_pairs = 0;
+  int* d_ovf = nullptr;
+  size_t d_ovf_n = 0;
+  // automatic hook choice: locality sample buffer and the last decision
+  unsigned long long* d_sample = nullptr;
+  unsigned long long* h_sample = nullptr;
+  const void* auto_rp = nullptr;
+  const void* auto_col = nullptr;
+  long long auto_V = -1, auto_m = -1;
+  int auto_w = 0;
   // staging buffers of cc_labels_csr_host
   void* d_rp = nullptr;
   size_t d_rp_bytes = 0;
@@ -33,6 +47,14 @@ struct cc_ctx {
 namespace {
 
 constexpr long long kDefaultTimeoutNs = 2000000000LL;
+constexpr int kDefaultChunkArcs = -1;
+constexpr int kDefaultTileVertices = 32768;
+constexpr int kMaxTileVertices = 32768;
+constexpr int kPlainBlock = 256;   // default block of the plain hook
+constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
+constexpr int kSampleThreads = 16384;
+constexpr double kLocalFractionForTiles = 0.5;
+constexpr int kPhaseSlots = 64;
 
 // Makes `device` current for the scope of a call and restores the caller's device after.
 struct DeviceGuard {
@@ -55,15 +77,67 @@ cc_status cuda_fail(cc_ctx* ctx, cudaError_t e, const char* where) {
 }
 
 void resolve_options(cc_options* o) {
-  if (o->block <= 0) o->block = 256;
   if (o->timeout_ns <= 0) o->timeout_ns = kDefaultTimeoutNs;
+  if (o->chunk_arcs == 0) o->chunk_arcs = kDefaultChunkArcs;
+}
+
+// Window of the two-phase hook for `want` vertices: a power of two, at least 256, no wider
+// than needed to cover V.
+int window_for(long long V, int want) {
+  int w = 256;
+  while (w < want && w < V) w <<= 1;
+  return w;
+}
+
+// Automatic hook choice (tile_vertices = 0): the two-phase hook pays off when most arcs join
+// vertices of the same window, i.e. when the vertex numbering has locality (meshes, road
+// networks in their natural order); otherwise the plain hook is used. A small sampling kernel
+// measures the fraction on the first call for a given graph (row_ptr, col_idx, V, n_arcs);
+// the answer is kept and reused while those stay the same. Only the speed depends on it.
+cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out) {
+  *w_out = 0;
+  if (p.V < 2 * 65536) return CC_OK;  // small graphs: the plain hook
+  const int w = window_for(p.V, kDefaultTileVertices);
+  if (ctx->auto_rp == p.rp && ctx->auto_col == p.col && ctx->auto_V == p.V && ctx->auto_m == p.m) {
+    *w_out = ctx->auto_w;
+    return CC_OK;
+  }
+  if (!ctx->d_sample) {
+    if (cudaMalloc(&ctx->d_sample, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_sample, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return CC_ERR_OOM;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->d_sample, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess) e = cc::launch_sample_locality(p, w, ctx->d_sample, kSampleThreads, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_sample, ctx->d_sample, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "locality sample");
+  const double total = (double)ctx->h_sample[1];
+  const double frac = total > 0 ? (double)ctx->h_sample[0] / total : 0.0;
+  ctx->auto_rp = p.rp;
+  ctx->auto_col = p.col;
+  ctx->auto_V = p.V;
+  ctx->auto_m = p.m;
+  ctx->auto_w = frac >= kLocalFractionForTiles ? w : 0;
+  *w_out = ctx->auto_w;
+  return CC_OK;
 }
 
 bool options_ok(const cc_options* o) {
   if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_MULTI_LAUNCH) return false;
-  if (o->segments < 0 || o->grid_blocks < 0 || o->reserved != 0) return false;
-  if (o->block != 0 && (o->block < 32 || o->block > 256 || o->block % 32 != 0)) return false;
-  if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC)) return false;
+  if (o->segments < 0 || o->grid_blocks < 0) return false;
+  if (o->chunk_arcs < -1 || (o->chunk_arcs > 0 && o->chunk_arcs % 32 != 0)) return false;
+  if (o->tile_vertices != 0 && o->tile_vertices != -1 &&
+      (o->tile_vertices < 256 || o->tile_vertices > kMaxTileVertices ||
+       (o->tile_vertices & (o->tile_vertices - 1)) != 0))
+    return false;
+  if (o->reserved != 0) return false;
+  if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0)) return false;
+  if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC | CC_FLAG_PHASE_TIMES)) return false;
   return true;
 }
 
@@ -91,10 +165,27 @@ cc_status read_and_clear_status(cc_ctx* ctx) {
   return CC_OK;
 }
 
+// Grows a context-owned device buffer to at least `n` elements of T.
+template <typename T>
+cudaError_t grow_buffer(T** buf, size_t* have, size_t n) {
+  if (n <= *have) return cudaSuccess;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), n * sizeof(T));
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  *have = n;
+  return cudaSuccess;
+}
+
 // Runs one single-graph problem on the context's stream.
 cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   const cc_options& o = ctx->opt;
-  const int block = o.block;
+  int block = o.block > 0 ? o.block : kPlainBlock;
   p.segments = o.segments > 0 ? o.segments : default_segments(p.m, p.V);
   if (p.m == 0) p.segments = 1;
 
@@ -102,6 +193,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   c.st = ctx->d_status;
   c.timeout_ns = o.timeout_ns;
   c.skip_arrival_block = -1;
+  c.chunk_arcs = o.chunk_arcs;
 
   // Work-proportional grid, capped by what is co-resident (the persistent kernel needs it).
   const long long work = std::max<long long>(p.V, p.m / 4);
@@ -109,11 +201,11 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   want = std::max<long long>(want, 1);
 
   cc_run_info info{};
-  info.block = block;
   info.segments = p.segments;
   int mode = o.mode == CC_MODE_AUTO ? CC_MODE_PERSISTENT : o.mode;
   info.mode = mode;
 
+  info.block = block;
   if (o.flags & CC_FLAG_VALIDATE) {
     cc::LaunchShape vs{(int)std::min<long long>(want, (long long)ctx->num_sms * 8), block};
     cudaError_t e = cc::launch_validate(p, c, vs, ctx->stream);
@@ -121,15 +213,68 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     info.launches += 1;
   }
 
+  // Two-phase hierarchical hook (CSR, persistent mode): windows of W vertices.
+  p.tile_w = 0;
+  p.unit_arcs = 0;
+  int w = 0;
+  if (p.kind == cc::kKindCsr && mode == CC_MODE_PERSISTENT && p.m > 0) {
+    if (o.tile_vertices > 0) {
+      w = window_for(p.V, o.tile_vertices);
+    } else if (o.tile_vertices == 0) {
+      const cc_status st = auto_window(ctx, p, &w);
+      if (st != CC_OK) return st;
+    }
+  }
+  if (w > 0) {
+    if (o.block <= 0) block = kTiledBlock;
+    p.tile_w = w;
+    // Worklist capacity: one pair per vertex (at least 2^20, at most one per arc). Windows
+    // whose appends overflow it are re-hooked arc by arc in phase B instead.
+    const size_t cap = (size_t)std::min<long long>(p.m, std::max<long long>(p.V, 1 << 20));
+    const size_t n_units = (size_t)((p.V + w - 1) / w);
+    if (grow_buffer(&ctx->d_wl, &ctx->d_wl_pairs, cap) != cudaSuccess ||
+        grow_buffer(&ctx->d_ovf, &ctx->d_ovf_n, n_units) != cudaSuccess) {
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error), "worklist allocation failed");
+      return CC_ERR_OOM;
+    }
+    c.tile_w = w;
+    c.wl = ctx->d_wl;
+    c.wl_cap = ctx->d_wl_pairs;
+    c.ovf_units = ctx->d_ovf;
+    c.ovf_cap = (int)std::min<size_t>(ctx->d_ovf_n, INT32_MAX);
+    c.segments_b = o.segments;
+  }
+
   if (mode == CC_MODE_PERSISTENT) {
-    const int per_sm = cc::persistent_blocks_per_sm(p, block);
+    // The requested block size must be co-resident at least once per SM; halve it until it is
+    // (a kernel variant may need more registers or shared memory than the request allows).
+    int per_sm = cc::persistent_blocks_per_sm(p, block);
+    while (per_sm <= 0 && block > 32) {
+      block /= 2;
+      per_sm = cc::persistent_blocks_per_sm(p, block);
+    }
+    info.block = block;
     if (per_sm <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "persistent occupancy");
+    want = std::max<long long>(1, (work + block - 1) / block);
     const long long cap = (long long)per_sm * ctx->num_sms;
     long long grid = o.grid_blocks > 0 ? std::min<long long>(o.grid_blocks, cap) : std::min(want, cap);
     cc::LaunchShape s{(int)grid, block};
     c.skip_arrival_block = ctx->skip_arrival_block;
     ctx->skip_arrival_block = -1;
-    cudaError_t e = cudaMemsetAsync(&ctx->d_status->bar, 0, sizeof(unsigned int), ctx->stream);
+    cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
+    if (e == cudaSuccess && (o.flags & CC_FLAG_PHASE_TIMES)) {
+      if (!ctx->d_phase && cudaMalloc(&ctx->d_phase, kPhaseSlots * sizeof(unsigned long long)) != cudaSuccess) {
+        ctx->d_phase = nullptr;
+        cudaGetLastError();
+        return CC_ERR_OOM;
+      }
+      e = cudaMemsetAsync(ctx->d_phase, 0, kPhaseSlots * sizeof(unsigned long long), ctx->stream);
+      c.phase_ns = ctx->d_phase;
+      c.phase_cap = kPhaseSlots;
+      ctx->phase_valid = true;
+    } else {
+      ctx->phase_valid = false;
+    }
     if (e == cudaSuccess) e = cc::launch_persistent(p, c, s, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
     info.grid_blocks = s.grid;
@@ -145,6 +290,8 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     info.grid_blocks = s.grid;
     info.launches += n;
   }
+  info.tile_vertices = p.tile_w;
+  info.worklist_capacity = p.tile_w > 0 ? (int64_t)ctx->d_wl_pairs : 0;
   ctx->last = info;
   if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
   return CC_OK;
@@ -158,7 +305,9 @@ void cc_default_options(cc_options* opt) {
   if (!opt) return;
   std::memset(opt, 0, sizeof(*opt));
   opt->mode = CC_MODE_AUTO;
-  opt->block = 256;
+  opt->block = 0;
+  opt->chunk_arcs = kDefaultChunkArcs;
+  opt->tile_vertices = 0;
   opt->timeout_ns = kDefaultTimeoutNs;
 }
 
@@ -347,6 +496,41 @@ cc_status cc_last_run_info(const cc_ctx* ctx, cc_run_info* info) {
   return CC_OK;
 }
 
+cc_status cc_last_phase_times(cc_ctx* ctx, int64_t* ns, int32_t cap, int32_t* n) {
+  if (!ctx || !ns || !n || cap <= 0) return CC_ERR_INVALID_ARG;
+  *n = 0;
+  if (!ctx->d_phase || !ctx->phase_valid) return CC_OK;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  unsigned long long host[kPhaseSlots];
+  cudaError_t e = cudaMemcpyAsync(host, ctx->d_phase, sizeof(host), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_last_phase_times");
+  // slot 0 = start, slots 1.. = barriers passed (until the first unused slot), last slot = end
+  int used = 1;
+  while (used < kPhaseSlots - 1 && host[used] != 0) ++used;
+  const int m = std::min(used + 1, (int)cap);
+  for (int i = 0; i < m; ++i) {
+    const unsigned long long t = (i == used) ? host[kPhaseSlots - 1] : host[i];
+    ns[i] = t >= host[0] ? (int64_t)(t - host[0]) : 0;
+  }
+  *n = m;
+  return CC_OK;
+}
+
+cc_status cc_last_worklist(cc_ctx* ctx, int64_t* pairs, int32_t* segments) {
+  if (!ctx || !pairs || !segments) return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  cc::DevStatus host;
+  cudaError_t e = cudaMemcpyAsync(&host, ctx->d_status, sizeof(host), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_last_worklist");
+  *pairs = (int64_t)host.report[0];
+  *segments = (int32_t)host.report[1];
+  return CC_OK;
+}
+
 const char* cc_last_error_message(const cc_ctx* ctx) { return ctx ? ctx->last_error : ""; }
 
 const char* cc_status_string(cc_status s) {
@@ -370,6 +554,11 @@ void cc_destroy(cc_ctx* ctx) {
     if (ctx->d_rp) cudaFree(ctx->d_rp);
     if (ctx->d_col) cudaFree(ctx->d_col);
     if (ctx->d_labels) cudaFree(ctx->d_labels);
+    if (ctx->d_phase) cudaFree(ctx->d_phase);
+    if (ctx->d_wl) cudaFree(ctx->d_wl);
+    if (ctx->d_ovf) cudaFree(ctx->d_ovf);
+    if (ctx->d_sample) cudaFree(ctx->d_sample);
+    if (ctx->h_sample) cudaFreeHost(ctx->h_sample);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     cudaGetLastError();

@@ -22,13 +22,17 @@ constexpr unsigned kFull = 0xffffffffu;
 // Device status block owned by the context. `bar` is zeroed before each
 // persistent launch; `error` is sticky until the host reads and clears it.
 struct DevStatus {
+  // per-launch fields (zeroed before every launch)
   unsigned int bar;
   unsigned int pad0;
+  unsigned long long counters[4];  // [0],[1] work counters; [2] worklist cursor; [3] overflowed units
+  unsigned long long report[2];    // [0] worklist pairs, [1] worklist segments (hierarchical hook)
+  // sticky error fields (cleared when the host reads them)
   int error;
   int error_where;
   long long error_info;
-  unsigned long long counters[4];
 };
+constexpr size_t kPerLaunchStatusBytes = 56;  // bar, pad0, counters, report
 
 // Where an error was raised (DevStatus::error_where).
 enum ErrorSite : int {
@@ -43,11 +47,25 @@ enum ErrorSite : int {
 // Status codes mirrored from cc.h (device code does not include the C header).
 enum DevError : int { kErrOutOfRange = 2, kErrTimeout = 5, kErrInternal = 6 };
 
+// Launch-wide control block passed by value to every kernel.
 struct Ctl {
-  DevStatus* st;
-  long long timeout_ns;
-  int skip_arrival_block;  // test hook (-1 = off)
+  DevStatus* st = nullptr;
+  long long timeout_ns = 2000000000LL;
+  int skip_arrival_block = -1;            // test hook (-1 = off)
+  int chunk_arcs = -1;                    // dynamic Atomic-Hook chunk (<= 0: one static slice per warp)
+  int tile_w = 0;                         // hierarchical hook window (vertices; 0 = plain hook)
+  long long unit_arcs = 0;                // (unused by the two-phase hook)
+  int2* wl = nullptr;                     // worklist of arcs left for the global hook
+  unsigned long long wl_cap = 0;
+  int* ovf_units = nullptr;               // windows whose worklist appends overflowed
+  int ovf_cap = 0;
+  int segments_b = 0;                     // segments of the global phase (0 = 2|E'|/|V|)
+  unsigned long long* phase_ns = nullptr; // optional per-barrier timestamps (block 0)
+  int phase_cap = 0;
 };
+
+// DevStatus::counters[0..1] are the work counters of the dynamically scheduled phases.
+constexpr int kWorkCounters = 2;
 
 // ---------------------------------------------------------------------------------------------
 // Memory access flavours.
@@ -136,6 +154,7 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
     }
     if (go && ld_relaxed(&c.st->error) != 0) go = 0;
     __threadfence();
+    if (c.phase_ns && blockIdx.x == 0 && (int)epoch < c.phase_cap - 1) c.phase_ns[epoch] = now_ns();
     s_go = go;
   }
   __syncthreads();
@@ -182,31 +201,129 @@ __device__ __forceinline__ void atomic_hook(int* pi, int u, int v, int V, const 
   }
 }
 
-// pi(v) <- v over [0, V), grid-strided.
+// Root of x, given px = pi(x) != x (the walk of find_root, resumed).
+__device__ __forceinline__ int root_from(int* pi, int x, int px) {
+  for (;;) {
+    const int gx = ld_pi(pi + px);
+    if (gx == px) return px;
+    st_pi(pi + x, gx);
+    x = gx;
+    px = ld_pi(pi + x);
+    if (px == x) return x;
+  }
+}
+
+// Root of a from its parent pa and grandparent ga (already loaded), halving one step if
+// the walk must go on.
+__device__ __forceinline__ int root_from2(int* pi, int a, int pa, int ga) {
+  if (pa == a) return a;
+  if (ga == pa) return pa;
+  st_pi(pi + a, ga);
+  const int pg = ld_pi(pi + ga);
+  return pg == ga ? ga : root_from(pi, ga, pg);
+}
+
+// Atomic-Hook of K independent edges per thread. The first two levels of all 2K root walks
+// are loaded together and all first CASes are issued together, so a thread keeps up to 2K
+// loads or K atomics in flight instead of one dependent chain; deeper walks and failed CASes
+// then finish one edge at a time exactly as in atomic_hook.
+template <int K>
+__device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const int (&v)[K], const bool (&live)[K],
+                                              int V, const Ctl& c) {
+  int pu[K], pv[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    pu[j] = live[j] ? ld_pi(pi + u[j]) : 0;
+    pv[j] = live[j] ? ld_pi(pi + v[j]) : 0;
+  }
+  int gu[K], gv[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    gu[j] = (live[j] && pu[j] != u[j]) ? ld_pi(pi + pu[j]) : pu[j];
+    gv[j] = (live[j] && pv[j] != v[j]) ? ld_pi(pi + pv[j]) : pv[j];
+  }
+  int H[K], L[K], old[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    H[j] = -1;
+    if (!live[j]) continue;
+    const int ru = root_from2(pi, u[j], pu[j], gu[j]);
+    const int rv = root_from2(pi, v[j], pv[j], gv[j]);
+    if (ru == rv) continue;
+    H[j] = ru > rv ? ru : rv;
+    L[j] = ru > rv ? rv : ru;
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if (H[j] >= 0) old[j] = atomicCAS(pi + H[j], H[j], L[j]);
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if (H[j] >= 0 && old[j] != H[j]) atomic_hook(pi, old[j], L[j], V, c);
+}
+
+// pi(v) <- v over [0, V), grid-strided; 16-byte stores when pi is 16-byte aligned.
 __device__ __forceinline__ void init_pi(int* pi, int V, long long tid, long long nthreads) {
-  for (long long v = tid; v < V; v += nthreads) pi[v] = (int)v;
+  if ((reinterpret_cast<uintptr_t>(pi) & 15) == 0) {
+    const long long n4 = V >> 2;
+    int4* p4 = reinterpret_cast<int4*>(pi);
+    for (long long q = tid; q < n4; q += nthreads) {
+      const int v = (int)(q << 2);
+      p4[q] = make_int4(v, v + 1, v + 2, v + 3);
+    }
+    for (long long v = (n4 << 2) + tid; v < V; v += nthreads) pi[v] = (int)v;
+  } else {
+    for (long long v = tid; v < V; v += nthreads) pi[v] = (int)v;
+  }
 }
 
 // Multi-Jump (Fig. 3, bottom; Section III-A): every vertex jumps pi(v) <- pi(pi(v)) until
 // pi(v) is a root, writing the intermediate value each step (optimisation (i)). Thread t
 // takes vertices t, t + T, ... so lower IDs, the tops of the trees, are served first
 // (optimisation (ii)). No hook runs concurrently, so roots are fixed during the phase.
-__device__ __forceinline__ void multi_jump(int* pi, int V, long long tid, long long nthreads, const Ctl& c) {
-  for (long long vv = tid; vv < V; vv += nthreads) {
-    const int v = (int)vv;
-    int p = ld_pi(pi + v);
-    if (p == v) continue;
-    int g = ld_pi(pi + p);
-    int guard = 0;
-    while (g != p) {
-      st_pi(pi + v, g);
-      p = g;
-      g = ld_pi(pi + p);
-      if (++guard > V) {
-        raise_error(c.st, kErrInternal, kSiteJumpGuard, (long long)v);
-        break;
-      }
+__device__ __forceinline__ void jump_from(int* pi, int v, int p, int g, int V, const Ctl& c) {
+  int guard = 0;
+  while (g != p) {
+    st_pi(pi + v, g);
+    p = g;
+    g = ld_pi(pi + p);
+    if (++guard > V) {
+      raise_error(c.st, kErrInternal, kSiteJumpGuard, (long long)v);
+      break;
     }
+  }
+}
+
+__device__ __forceinline__ int4 ld_pi4(const int* p) {
+  int4 v;
+  asm volatile("ld.global.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void multi_jump(int* pi, int V, long long tid, long long nthreads, const Ctl& c) {
+  long long first_scalar = 0;
+  if ((reinterpret_cast<uintptr_t>(pi) & 15) == 0) {
+    // Four consecutive vertices per thread: one 16-byte load of pi(v..v+3), then their four
+    // grandparent loads issued together before any of the (rare) longer walks.
+    const long long n4 = V >> 2;
+    for (long long q = tid; q < n4; q += nthreads) {
+      const int v = (int)(q << 2);
+      const int4 p = ld_pi4(pi + v);
+      const int g0 = p.x != v ? ld_pi(pi + p.x) : p.x;
+      const int g1 = p.y != v + 1 ? ld_pi(pi + p.y) : p.y;
+      const int g2 = p.z != v + 2 ? ld_pi(pi + p.z) : p.z;
+      const int g3 = p.w != v + 3 ? ld_pi(pi + p.w) : p.w;
+      if (g0 != p.x) jump_from(pi, v, p.x, g0, V, c);
+      if (g1 != p.y) jump_from(pi, v + 1, p.y, g1, V, c);
+      if (g2 != p.z) jump_from(pi, v + 2, p.z, g2, V, c);
+      if (g3 != p.w) jump_from(pi, v + 3, p.w, g3, V, c);
+    }
+    first_scalar = n4 << 2;
+  }
+  for (long long vv = first_scalar + tid; vv < V; vv += nthreads) {
+    const int v = (int)vv;
+    const int p = ld_pi(pi + v);
+    if (p == v) continue;
+    jump_from(pi, v, p, ld_pi(pi + p), V, c);
   }
 }
 
@@ -240,6 +357,34 @@ __device__ __forceinline__ int warp_row_search(const OffT* rp, int lo, int hi, O
   return lo + (31 - __clz(m));
 }
 
+// Root of x in a CTA-local parent array (shared memory), with path halving. The local array
+// obeys the same invariant as pi (lp(x) <= x), so the walk ends within W steps.
+__device__ __forceinline__ int lfind(volatile int* lp, int x) {
+  int px = lp[x];
+  while (px != x) {
+    const int gx = lp[px];
+    if (gx == px) return px;
+    lp[x] = gx;
+    x = gx;
+    px = lp[x];
+  }
+  return x;
+}
+
+// Atomic-Hook of local indices (a, b) on the shared-memory parent array.
+__device__ __forceinline__ void local_hook(int* lp, int a, int b) {
+  volatile int* vlp = lp;
+  int ra = lfind(vlp, a), rb = lfind(vlp, b);
+  while (ra != rb) {
+    const int H = ra > rb ? ra : rb;
+    const int L = ra > rb ? rb : ra;
+    const int old = atomicCAS(lp + H, H, L);
+    if (old == H) return;
+    ra = lfind(vlp, old);
+    rb = lfind(vlp, L);
+  }
+}
+
 // Number of lanes l whose row end e_l (non-decreasing in l) is <= a (0..32).
 template <typename OffT>
 __device__ __forceinline__ int window_count(OffT e, OffT a) {
@@ -254,75 +399,389 @@ __device__ __forceinline__ int window_count(OffT e, OffT a) {
   return pos;
 }
 
-// Atomic-Hook over the arcs [a0, a1) of a CSR graph (one segment E_i of Fig. 4). Each warp
-// takes one contiguous slice of the segment and walks it 32 arcs at a time (coalesced
-// col_idx reads). The source row of every arc comes from a window of 32 row offsets held
-// one per lane: lane l holds the end of row r + l, and an arc's row is r + (number of window
-// ends <= arc). A warp searches row_ptr only at the start of its slice and when a batch runs
-// past its window (rows with few or no arcs).
+// Row of the arc aq of this lane, from a window of 32 row ends held one per lane: lane l
+// holds the end of row r + l, so the row is r + (number of window ends <= aq). When a lane's
+// arc lies past the window (rows with few or no arcs), the warp searches row_ptr from r + 32.
+// Returns V if no row exists (only when row_ptr[V] != n_arcs). Afterwards r is the row of the
+// arc of lane `last` (the batch's last valid lane), the start of the next window.
+template <typename OffT>
+__device__ __forceinline__ int resolve_row(const OffT* __restrict__ rp, int V, int& r, OffT aq, bool valid,
+                                           int last) {
+  const int lane = threadIdx.x & 31;
+  const long long wi = (long long)r + 1 + lane;
+  OffT e = ld_ro(rp + (wi < V ? wi : V));
+  int cnt = window_count<OffT>(e, aq);
+  int u = cnt < 32 ? r + cnt : -1;
+  unsigned pend = __ballot_sync(kFull, valid && u < 0);
+  while (pend) {
+    if ((long long)r + 32 >= V) {
+      if (valid && u < 0) u = V;
+      break;
+    }
+    const int first = __ffs(pend) - 1;
+    const OffT amin = __shfl_sync(kFull, aq, first);
+    r = warp_row_search<OffT>(rp, r + 32, V, amin);
+    const long long wj = (long long)r + 1 + lane;
+    e = ld_ro(rp + (wj < V ? wj : V));
+    cnt = window_count<OffT>(e, aq);
+    if (valid && u < 0 && cnt < 32) u = r + cnt;
+    pend = __ballot_sync(kFull, valid && u < 0);
+  }
+  const int nr = __shfl_sync(kFull, u, last);
+  r = nr < V ? nr : V;
+  return u;
+}
+
+// Per-warp staging buffer in shared memory for the worklist of the two-phase hook: arcs are
+// appended by ballot (no atomics) and flushed to the global worklist with one atomic per flush.
+constexpr int kSinkPairs = 128;
+
+struct WarpSink {
+  int2* buf;  // kSinkPairs entries in shared memory, private to the warp
+  int count;  // warp-uniform
+};
+
+__device__ __forceinline__ void sink_flush(WarpSink& s, const Ctl& c, volatile int* ovf) {
+  if (s.count == 0) return;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&c.st->counters[2], (unsigned long long)s.count);
+  base = __shfl_sync(kFull, base, 0);
+  for (int i = lane; i < s.count; i += 32) {
+    const unsigned long long pos = base + (unsigned long long)i;
+    if (pos < c.wl_cap) c.wl[pos] = s.buf[i];
+    else *ovf = 1;
+  }
+  __syncwarp();
+  s.count = 0;
+}
+
+__device__ __forceinline__ void sink_push(WarpSink& s, bool take, int u, int v, const Ctl& c, volatile int* ovf) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int n = __popc(m);
+  if (s.count + n > kSinkPairs) sink_flush(s, c, ovf);
+  const int lane = threadIdx.x & 31;
+  if (take) s.buf[s.count + __popc(m & ((1u << lane) - 1u))] = make_int2(u, v);
+  s.count += n;
+}
+
+// Atomic-Hook over the arcs [t0, t1) of a CSR graph by one warp, 32 x K arcs per step: lane l
+// takes arcs b + l + 32 j, j < K (each j a coalesced read of col_idx), and the next step's
+// arcs are loaded before the current ones are hooked, so the arc stream stays in flight.
 // SYM: the CSR holds both directions of every edge, so arcs with u > v are skipped.
+// TILED (phase A of the two-phase hook): an arc with both endpoints in [wbase, wbase + W) is
+// hooked on the shared-memory parent array lp; any other arc goes to the worklist through the
+// warp's sink. Otherwise every arc is Atomic-Hooked on pi, K at a time.
+// lo_row is a row with rp[lo_row] <= t0.
+template <typename OffT, bool SYM, bool TILED, int K>
+__device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                               int V, OffT t0, OffT t1, const Ctl& c, int lo_row,
+                                               int* lp = nullptr, int wbase = 0, int W = 0,
+                                               WarpSink* sink = nullptr, volatile int* ovf = nullptr) {
+  const int lane = threadIdx.x & 31;
+  int r = warp_row_search<OffT>(rp, lo_row, V, t0);
+  int vn[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const OffT a = t0 + 32 * j + lane;
+    vn[j] = a < t1 ? ld_stream(col + a) : 0;
+  }
+  for (OffT b = t0; b < t1; b += 32 * K) {
+    int v[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = vn[j];
+    const OffT nb = b + 32 * K;
+    if (nb < t1) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const OffT a = nb + 32 * j + lane;
+        vn[j] = a < t1 ? ld_stream(col + a) : 0;
+      }
+    }
+    int u[K];
+    bool live[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const OffT bj = b + 32 * j;
+      u[j] = -1;
+      live[j] = false;
+      if (bj < t1) {  // warp-uniform
+        const OffT a = bj + lane;
+        const bool valid = a < t1;
+        const long long rem = (long long)(t1 - bj) - 1;
+        u[j] = resolve_row<OffT>(rp, V, r, valid ? a : bj, valid, rem < 31 ? (int)rem : 31);
+        if (valid) {
+          const bool in_range = (unsigned)v[j] < (unsigned)V && (unsigned)u[j] < (unsigned)V;
+          if (!in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a);
+          live[j] = in_range && !(SYM ? (u[j] >= v[j]) : (u[j] == v[j]));
+        }
+      }
+    }
+    if (TILED) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const bool local =
+            live[j] && (unsigned)(u[j] - wbase) < (unsigned)W && (unsigned)(v[j] - wbase) < (unsigned)W;
+        if (local) local_hook(lp, u[j] - wbase, v[j] - wbase);
+        sink_push(*sink, live[j] && !local, u[j], v[j], c, ovf);
+      }
+    } else {
+      atomic_hook_k<K>(pi, u, v, live, V, c);
+    }
+  }
+  if (TILED) sink_flush(*sink, c, ovf);
+}
+
+constexpr int kHookK = 1;   // arcs per lane per step of the plain hook
+constexpr int kPairK = 4;   // worklist pairs per thread per step of phase B
+
+// Atomic-Hook over the arcs [a0, a1) of a CSR graph (one segment E_i of Fig. 4). With
+// c.chunk_arcs > 0, warps take chunks of that many arcs from the work counter `ctr` (zeroed
+// before the phase) until the segment is exhausted; otherwise each warp takes one fixed
+// contiguous slice.
 template <typename OffT, bool SYM>
 __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                               int V, OffT a0, OffT a1, long long tid, long long nthreads,
-                                              const Ctl& c) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = tid >> 5;
-  const long long nwarps = nthreads >> 5;
+                                              unsigned long long* ctr, const Ctl& c) {
   const OffT len = a1 - a0;
-  const OffT t0 = a0 + split_point<OffT>(len, nwarps, warp);
-  const OffT t1 = a0 + split_point<OffT>(len, nwarps, warp + 1);
-  if (t0 >= t1) return;  // warp-uniform
-  int r = warp_row_search<OffT>(rp, 0, V, t0);
-  for (OffT b = t0; b < t1; b += 32) {
-    const OffT a = b + lane;
-    const bool valid = a < t1;
-    const OffT aq = valid ? a : b;
-    const int v = valid ? ld_stream(col + a) : 0;
-    const long long wi = (long long)r + 1 + lane;
-    OffT e = ld_ro(rp + (wi < V ? wi : V));
-    int cnt = window_count<OffT>(e, aq);
-    int u = cnt < 32 ? r + cnt : -1;
-    unsigned pend = __ballot_sync(kFull, valid && u < 0);
-    while (pend) {
-      if ((long long)r + 32 >= V) {
-        // Only reachable when row_ptr[V] != n_arcs: the remaining arcs have no row.
-        if (valid && u < 0) u = V;
-        break;
-      }
-      const int first = __ffs(pend) - 1;
-      const OffT amin = __shfl_sync(kFull, aq, first);
-      r = warp_row_search<OffT>(rp, r + 32, V, amin);
-      const long long wj = (long long)r + 1 + lane;
-      e = ld_ro(rp + (wj < V ? wj : V));
-      cnt = window_count<OffT>(e, aq);
-      if (valid && u < 0 && cnt < 32) u = r + cnt;
-      pend = __ballot_sync(kFull, valid && u < 0);
-    }
-    const long long last_valid = (long long)(t1 - b) - 1;
-    r = __shfl_sync(kFull, u, last_valid < 31 ? (int)last_valid : 31);
-    r = r < V ? r : V;
-    if (!valid) continue;
-    if ((unsigned)v >= (unsigned)V || (unsigned)u >= (unsigned)V) {
-      raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a);
-      continue;
-    }
-    if (SYM ? (u >= v) : (u == v)) continue;
-    atomic_hook(pi, u, v, V, c);
+  if (len <= 0) return;
+  if (c.chunk_arcs <= 0 || ctr == nullptr) {
+    const long long warp = tid >> 5, nwarps = nthreads >> 5;
+    const OffT t0 = a0 + split_point<OffT>(len, nwarps, warp);
+    const OffT t1 = a0 + split_point<OffT>(len, nwarps, warp + 1);
+    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, 0);
+    return;
+  }
+  const OffT C = (OffT)c.chunk_arcs;
+  const unsigned long long n_chunks = (unsigned long long)((len + C - 1) / C);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1ull);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= n_chunks) break;
+    const OffT t0 = a0 + (OffT)t * C;
+    const OffT t1 = (len - (OffT)t * C) > C ? t0 + C : a1;
+    hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, 0);
   }
 }
 
-// Atomic-Hook over edges [e0, e1) of an edge list.
+// Bytes of dynamic shared memory of the two-phase hook for a block of `block` threads.
+__host__ __device__ __forceinline__ size_t tiled_smem_bytes(int W, int block) {
+  return (size_t)W * sizeof(int) + (size_t)(block / 32) * kSinkPairs * sizeof(int2);
+}
+
+// Rows with more arcs than this are walked by a whole warp in phase A.
+constexpr int kHeavyRow = 32;
+// Arcs of a row loaded together in phase A.
+constexpr int kGroup = 4;
+
+// Arc span [x0, x1) of window row i (0, 0 past the end of the warp's rows).
+template <typename OffT>
+__device__ __forceinline__ void load_row_span(const OffT* __restrict__ rp, int w0, int i, int end, OffT& x0,
+                                              OffT& x1) {
+  if (i < end) {
+    x0 = ld_ro(rp + w0 + i);
+    x1 = ld_ro(rp + w0 + i + 1);
+  } else {
+    x0 = 0;
+    x1 = 0;
+  }
+}
+
+// Offsets inconsistent with n_arcs are reported and replaced by an empty span, so no read
+// of col_idx leaves [0, n_arcs).
+template <typename OffT>
+__device__ __forceinline__ void check_span(OffT& x0, OffT& x1, OffT nnz, int u, const Ctl& c) {
+  if (!(x0 >= 0 && x0 <= x1 && x1 <= nnz)) {
+    raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)u);
+    x0 = 0;
+    x1 = 0;
+  }
+}
+
+// Arcs x0 + kGroup*g + j (j < kGroup) of a row, 0 beyond its end.
+template <typename OffT>
+__device__ __forceinline__ void load_group(const int* __restrict__ col, OffT x0, OffT x1, int g, int (&v)[kGroup]) {
+#pragma unroll
+  for (int j = 0; j < kGroup; ++j) {
+    const OffT a = x0 + (OffT)(g * kGroup + j);
+    v[j] = a < x1 ? ld_stream(col + a) : 0;
+  }
+}
+
+// Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window.
+template <bool SYM>
+__device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, long long a, int V, int w0, int nrows,
+                                            int* lp, WarpSink& sink, volatile int* ovf, const Ctl& c) {
+  const bool in_range = has && (unsigned)v < (unsigned)V;
+  if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+  const bool live = in_range && (SYM ? (v > u) : (v != u));
+  const bool local = live && (unsigned)(v - w0) < (unsigned)nrows;
+  if (local) local_hook(lp, i, v - w0);
+  sink_push(sink, live && !local, u, v, c, ovf);
+}
+
+// Two-phase hierarchical Atomic-Hook, phase A. The vertices are cut into windows of W
+// consecutive IDs; a CTA takes windows from work counter 0. For window [w0, w0 + W) it keeps a
+// local parent array lp in shared memory and streams the arcs of the window's rows once, one
+// row per lane (rows of more than kHeavyRow arcs by the whole warp): an arc with both
+// endpoints in the window is Atomic-Hooked on lp (the high-to-low CAS rule on local indices);
+// any other arc goes to the worklist. The local trees are then compressed and written as the
+// window's part of pi with plain stores: pi(x) = w0 + local root of x, the minimum vertex of
+// x's local component. Every vertex belongs to exactly one window, so this also initialises
+// pi, and no two CTAs write the same entry. If the worklist is full, the window is recorded as
+// overflowed and phase B hooks all of its arcs again on pi.
+template <typename OffT, bool SYM>
+__device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                              int V, OffT nnz, int* smem, const Ctl& c) {
+  __shared__ unsigned long long s_unit;
+  __shared__ int s_ovf;
+  const int W = c.tile_w;
+  int* lp = smem;
+  const long long n_units = ((long long)V + W - 1) / W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  WarpSink sink;
+  sink.buf = reinterpret_cast<int2*>(smem + W) + warp * kSinkPairs;
+  sink.count = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = atomicAdd(&c.st->counters[0], 1ull);
+      s_ovf = 0;
+    }
+    __syncthreads();
+    const unsigned long long k = s_unit;
+    if (k >= (unsigned long long)n_units) break;
+    const int w0 = (int)(k * (unsigned long long)W);
+    const int nrows = (V - w0) < W ? (V - w0) : W;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = i;
+    __syncthreads();
+    // Warps take 32-row chunks (one row per lane) in an interleaved order, so the CTA sweeps
+    // the window roughly in ID order and new vertices mostly join components that already have
+    // short paths to their roots. Loads run ahead of the hooks: row offsets two chunks ahead,
+    // the first kGroup arcs of each row one chunk ahead.
+    const int step = nwarps * 32;
+    const int r_begin = warp * 32;
+    const int r_end = nrows;
+    if (r_begin < r_end) {  // warp-uniform
+      OffT a0, a1, na0, na1;
+      int v[kGroup], nv[kGroup];
+      load_row_span<OffT>(rp, w0, r_begin + lane, r_end, a0, a1);
+      check_span<OffT>(a0, a1, nnz, w0 + r_begin + lane, c);
+      load_group<OffT>(col, a0, a1, 0, v);
+      load_row_span<OffT>(rp, w0, r_begin + step + lane, r_end, na0, na1);
+      for (int base = r_begin; base < r_end; base += step) {
+        check_span<OffT>(na0, na1, nnz, w0 + base + step + lane, c);
+        load_group<OffT>(col, na0, na1, 0, nv);
+        OffT nna0, nna1;
+        load_row_span<OffT>(rp, w0, base + 2 * step + lane, r_end, nna0, nna1);
+        const int i = base + lane;
+        const int u = w0 + i;
+        const long long deg = (long long)(a1 - a0);
+        const bool heavy = deg > kHeavyRow;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+          phase_a_arc<SYM>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, &s_ovf, c);
+        const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
+        for (int g = 1; g * kGroup < maxdeg; ++g) {
+          int w[kGroup];
+          load_group<OffT>(col, a0, heavy ? a0 : a1, g, w);
+#pragma unroll
+          for (int j = 0; j < kGroup; ++j)
+            phase_a_arc<SYM>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0,
+                             nrows, lp, sink, &s_ovf, c);
+        }
+        unsigned hv = __ballot_sync(kFull, heavy);
+        while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
+          const int h = __ffs(hv) - 1;
+          hv &= hv - 1;
+          const int hi = __shfl_sync(kFull, i, h);
+          const OffT h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
+          for (OffT bb = h0; bb < h1; bb += 32) {
+            const OffT a = bb + lane;
+            const bool has = a < h1;
+            const int vv = has ? ld_stream(col + a) : 0;
+            phase_a_arc<SYM>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, &s_ovf, c);
+          }
+        }
+        a0 = na0;
+        a1 = na1;
+        na0 = nna0;
+        na1 = nna1;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) v[j] = nv[j];
+      }
+    }
+    sink_flush(sink, c, &s_ovf);
+    __syncthreads();
+    volatile int* vlp = lp;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) pi[w0 + i] = w0 + lfind(vlp, i);
+    if (threadIdx.x == 0 && s_ovf) {
+      const unsigned long long j = atomicAdd(&c.st->counters[3], 1ull);
+      if (j < (unsigned long long)c.ovf_cap) c.ovf_units[j] = (int)k;
+    }
+    __syncthreads();
+  }
+}
+
+// Phase B, one segment: Atomic-Hook on pi of worklist pairs [p0, p1) (K per thread, each j a
+// coalesced read) and, when `overflowed` is set, of every arc of the windows listed as
+// overflowed (one CTA per window).
+template <typename OffT, bool SYM>
+__device__ __forceinline__ void tiled_phase_b(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                              int V, OffT nnz, unsigned long long p0, unsigned long long p1,
+                                              bool overflowed, unsigned long long n_ovf, long long tid,
+                                              long long nthreads, const Ctl& c) {
+  constexpr int K = kPairK;
+  const unsigned long long T = (unsigned long long)nthreads;
+  for (unsigned long long base = p0 + (unsigned long long)tid; base < p1; base += T * K) {
+    int u[K], v[K];
+    bool live[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const unsigned long long i = base + (unsigned long long)j * T;
+      live[j] = i < p1;
+      const int2 e = live[j] ? c.wl[i] : make_int2(0, 0);
+      u[j] = e.x;
+      v[j] = e.y;
+    }
+    atomic_hook_k<K>(pi, u, v, live, V, c);
+  }
+  if (!overflowed) return;
+  const int W = c.tile_w;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (unsigned long long j = blockIdx.x; j < n_ovf; j += gridDim.x) {
+    const int w0 = c.ovf_units[j] * W;
+    const int nrows = (V - w0) < W ? (V - w0) : W;
+    const OffT u0 = ld_ro(rp + w0), u1 = ld_ro(rp + w0 + nrows);
+    if (!(u0 >= 0 && u0 <= u1 && u1 <= nnz)) continue;
+    const OffT t0 = u0 + split_point<OffT>(u1 - u0, nwarps, warp);
+    const OffT t1 = u0 + split_point<OffT>(u1 - u0, nwarps, warp + 1);
+    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, w0);
+  }
+}
+
+// Atomic-Hook over edges [e0, e1) of an edge list, K edges per thread per step.
 __device__ __forceinline__ void hook_coo_edges(const int* __restrict__ src, const int* __restrict__ dst, int* pi,
                                                int V, long long e0, long long e1, long long tid,
                                                long long nthreads, const Ctl& c) {
-  for (long long i = e0 + tid; i < e1; i += nthreads) {
-    const int u = ld_stream(src + i);
-    const int v = ld_stream(dst + i);
-    if ((unsigned)u >= (unsigned)V || (unsigned)v >= (unsigned)V) {
-      raise_error(c.st, kErrOutOfRange, kSiteHookArc, i);
-      continue;
+  constexpr int K = kHookK;
+  for (long long base = e0 + tid; base < e1; base += nthreads * K) {
+    int u[K], v[K];
+    bool live[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const long long i = base + (long long)j * nthreads;
+      const bool valid = i < e1;
+      u[j] = valid ? ld_stream(src + i) : 0;
+      v[j] = valid ? ld_stream(dst + i) : 0;
+      const bool in_range = (unsigned)u[j] < (unsigned)V && (unsigned)v[j] < (unsigned)V;
+      if (valid && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, i);
+      live[j] = valid && in_range && u[j] != v[j];
     }
-    if (u != v) atomic_hook(pi, u, v, V, c);
+    atomic_hook_k<K>(pi, u, v, live, V, c);
   }
 }
 

@@ -22,6 +22,8 @@ struct Problem {
   long long m;         // arcs (CSR) or edges (COO)
   int segments;
   bool sym;
+  int tile_w;          // > 0: hierarchical hook with this window (CSR only)
+  long long unit_arcs; // hierarchical hook work unit
 };
 
 enum : int { kKindCsr = 1, kKindCoo = 2 };
@@ -31,9 +33,12 @@ struct LaunchShape {
   int block;
 };
 
-// Blocks of the persistent kernel that fit on one SM at `block` threads (0 if it cannot run).
+// Blocks of the persistent kernel that fit on one SM at `block` threads (0 if it cannot run),
+// including the dynamic shared memory of the hierarchical hook.
 int persistent_blocks_per_sm(const Problem& p, int block);
 int stage_blocks_per_sm(const Problem& p, int block);
+// Dynamic shared memory of a launch for problem p.
+size_t dynamic_smem_bytes(const Problem& p, int block);
 
 // One cooperative launch running init + all segments (Hook, barrier, Multi-Jump, barrier).
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
@@ -41,6 +46,10 @@ cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cud
 // Fig. 4 as printed: init, then per segment one Hook launch and one Multi-Jump launch.
 // Returns the number of launches issued in *launches.
 cudaError_t launch_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream, int* launches);
+
+// Locality sample: out[0] += sampled arcs with both ends in one window of W vertices,
+// out[1] += sampled arcs (out must be zeroed by the caller).
+cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* out, int threads, cudaStream_t stream);
 
 // Device checks of CSR offsets and endpoints (CC_FLAG_VALIDATE).
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);

@@ -1,39 +1,93 @@
 // Single-graph kernels: the persistent driver of Fig. 4 (one cooperative launch, grid
 // barriers between Hook and Multi-Jump phases) and the per-phase kernels of the printed
-// host loop, for CSR (int32 / int64 offsets, plain or symmetrised) and COO inputs.
+// host loop, for CSR (int32 / int64 offsets, plain or symmetrised, plain or hierarchical
+// hook) and COO inputs.
 #include "cc_internal.h"
 
 namespace cc {
 
 namespace {
 
+constexpr int kMaxBlock = 1024;
+
 __device__ __forceinline__ long long global_tid() {
   return (long long)blockIdx.x * blockDim.x + threadIdx.x;
 }
 __device__ __forceinline__ long long global_threads() { return (long long)gridDim.x * blockDim.x; }
 
-// Adaptive Hook-Compress (Fig. 4) over the arcs of a CSR graph, in one launch:
-//   init pi; for i in 1..s: Atomic-Hook(E_i); barrier; Multi-Jump(V); barrier.
-template <typename OffT, bool SYM>
-__global__ void __launch_bounds__(256) k_csr_persistent(const OffT* __restrict__ rp, const int* __restrict__ col,
-                                                        int* pi, int V, OffT nnz, int s, Ctl c) {
+__device__ __forceinline__ void phase_start(const Ctl& c) {
+  if (c.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) c.phase_ns[0] = now_ns();
+}
+__device__ __forceinline__ void phase_end(const Ctl& c) {
+  if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + (c.phase_cap - 1), now_ns());
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Adaptive Hook-Compress (Fig. 4) over the arcs of a CSR graph, in one launch.
+// Plain:  init pi; for i in 1..s: Atomic-Hook(E_i); barrier; Multi-Jump(V); barrier.
+//         Hook phase i takes its work from counter i % 2; thread 0 zeroes the other counter
+//         during the phase, and the barriers in between publish the reset before its next use.
+// TILED:  phase A (window-local hooks in shared memory, pi written, worklist E' built);
+//         barrier; then Fig. 4 over E': s' = 2|E'|/|V| segments, each Atomic-Hook on pi
+//         followed by Multi-Jump(V).
+template <typename OffT, bool SYM, bool TILED>
+__device__ __forceinline__ void csr_persistent_body(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                    int* pi, int V, OffT nnz, int s, int* lp, const Ctl& c) {
   if (ld_relaxed(&c.st->error) != 0) return;  // a pending error stops all device work
   unsigned epoch = 0;
   const long long tid = global_tid(), nt = global_threads();
+  if (TILED) {
+    tiled_phase_a<OffT, SYM>(rp, col, pi, V, nnz, lp, c);
+    if (!grid_sync(c, epoch)) return;
+    const unsigned long long cur = ld_volatile_u64(&c.st->counters[2]);
+    const unsigned long long n_pairs = cur < c.wl_cap ? cur : c.wl_cap;
+    unsigned long long n_ovf = ld_volatile_u64(&c.st->counters[3]);
+    n_ovf = n_ovf < (unsigned long long)c.ovf_cap ? n_ovf : (unsigned long long)c.ovf_cap;
+    if (n_pairs == 0 && n_ovf == 0) return;  // every tree is already a star rooted at its minimum
+    long long s2 = c.segments_b;
+    if (s2 <= 0) s2 = (long long)((2.0 * (double)n_pairs) / (double)V + 0.5);
+    s2 = s2 < 1 ? 1 : (s2 > 4096 ? 4096 : s2);
+    if (tid == 0) {
+      c.st->report[0] = n_pairs;
+      c.st->report[1] = (unsigned long long)s2;
+    }
+    for (long long i = 0; i < s2; ++i) {
+      tiled_phase_b<OffT, SYM>(rp, col, pi, V, nnz, split_point<unsigned long long>(n_pairs, s2, i),
+                               split_point<unsigned long long>(n_pairs, s2, i + 1), i == 0, n_ovf, tid, nt, c);
+      if (!grid_sync(c, epoch)) return;
+      multi_jump(pi, V, tid, nt, c);
+      if (i + 1 < s2 && !grid_sync(c, epoch)) return;
+    }
+    return;
+  }
   init_pi(pi, V, tid, nt);
   if (!grid_sync(c, epoch)) return;
   for (int i = 0; i < s; ++i) {
+    if (tid == 0) c.st->counters[(i + 1) % kWorkCounters] = 0ull;
     const OffT a0 = split_point<OffT>(nnz, s, i);
     const OffT a1 = split_point<OffT>(nnz, s, i + 1);
-    hook_csr_arcs<OffT, SYM>(rp, col, pi, V, a0, a1, tid, nt, c);
+    hook_csr_arcs<OffT, SYM>(rp, col, pi, V, a0, a1, tid, nt, &c.st->counters[i % kWorkCounters], c);
     if (!grid_sync(c, epoch)) return;
     multi_jump(pi, V, tid, nt, c);
     if (i + 1 < s && !grid_sync(c, epoch)) return;
   }
 }
 
-__global__ void __launch_bounds__(256) k_coo_persistent(const int* __restrict__ src, const int* __restrict__ dst,
-                                                        int* pi, int V, long long E, int s, Ctl c) {
+template <typename OffT, bool SYM, bool TILED>
+__global__ void __launch_bounds__(kMaxBlock, TILED ? 1 : 2) k_csr_persistent(const OffT* __restrict__ rp,
+                                                              const int* __restrict__ col, int* pi, int V, OffT nnz,
+                                                              int s, Ctl c) {
+  extern __shared__ int dyn_smem[];
+  phase_start(c);
+  csr_persistent_body<OffT, SYM, TILED>(rp, col, pi, V, nnz, s, dyn_smem, c);
+  phase_end(c);
+}
+
+__device__ __forceinline__ void coo_persistent_body(const int* __restrict__ src, const int* __restrict__ dst,
+                                                    int* pi, int V, long long E, int s, const Ctl& c) {
   if (ld_relaxed(&c.st->error) != 0) return;
   unsigned epoch = 0;
   const long long tid = global_tid(), nt = global_threads();
@@ -48,36 +102,75 @@ __global__ void __launch_bounds__(256) k_coo_persistent(const int* __restrict__ 
   }
 }
 
-// ----- per-phase kernels (the host loop of Fig. 4) -----
+__global__ void __launch_bounds__(kMaxBlock, 1) k_coo_persistent(const int* __restrict__ src,
+                                                              const int* __restrict__ dst, int* pi, int V,
+                                                              long long E, int s, Ctl c) {
+  phase_start(c);
+  coo_persistent_body(src, dst, pi, V, E, s, c);
+  phase_end(c);
+}
 
-__global__ void __launch_bounds__(256) k_init(int* pi, int V, Ctl c) {
+// ----- per-phase kernels (the host loop of Fig. 4) -----
+// Work counter 0 is zeroed by the kernel before each hook kernel (init or jump); the
+// launches are stream-ordered, so no hook kernel overlaps a reset.
+
+__global__ void __launch_bounds__(kMaxBlock) k_init(int* pi, int V, Ctl c) {
+  if (global_tid() == 0) c.st->counters[0] = 0ull;
   if (ld_relaxed(&c.st->error) != 0) return;
   init_pi(pi, V, global_tid(), global_threads());
 }
 
 template <typename OffT, bool SYM>
-__global__ void __launch_bounds__(256) k_hook_csr(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
-                                                  int V, OffT a0, OffT a1, Ctl c) {
+__global__ void __launch_bounds__(kMaxBlock) k_hook_csr(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                        int* pi, int V, OffT a0, OffT a1, Ctl c) {
   if (ld_relaxed(&c.st->error) != 0) return;
-  hook_csr_arcs<OffT, SYM>(rp, col, pi, V, a0, a1, global_tid(), global_threads(), c);
+  hook_csr_arcs<OffT, SYM>(rp, col, pi, V, a0, a1, global_tid(), global_threads(), &c.st->counters[0], c);
 }
 
-__global__ void __launch_bounds__(256) k_hook_coo(const int* __restrict__ src, const int* __restrict__ dst, int* pi,
-                                                  int V, long long e0, long long e1, Ctl c) {
+__global__ void __launch_bounds__(kMaxBlock) k_hook_coo(const int* __restrict__ src, const int* __restrict__ dst,
+                                                        int* pi, int V, long long e0, long long e1, Ctl c) {
   if (ld_relaxed(&c.st->error) != 0) return;
   hook_coo_edges(src, dst, pi, V, e0, e1, global_tid(), global_threads(), c);
 }
 
-__global__ void __launch_bounds__(256) k_jump(int* pi, int V, Ctl c) {
+__global__ void __launch_bounds__(kMaxBlock) k_jump(int* pi, int V, Ctl c) {
+  if (global_tid() == 0) c.st->counters[0] = 0ull;
   if (ld_relaxed(&c.st->error) != 0) return;
   multi_jump(pi, V, global_tid(), global_threads(), c);
+}
+
+// ----- locality sample (automatic choice of the hook variant) -----
+// Thread t looks at the middle arc of row t * V / T and counts it as local when both ends lie
+// in the same window of W vertices. out[0] += local arcs, out[1] += sampled arcs.
+template <typename OffT>
+__global__ void __launch_bounds__(256) k_sample_locality(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                         int V, OffT nnz, int W, unsigned long long* out) {
+  const long long t = global_tid(), T = global_threads();
+  const int u = (int)((t * (long long)V) / T);
+  bool sampled = false, local = false;
+  if (u < V) {
+    const OffT a0 = rp[u], a1 = rp[u + 1];
+    if (a0 >= 0 && a0 < a1 && a1 <= nnz) {
+      const int v = col[a0 + (a1 - a0) / 2];
+      if ((unsigned)v < (unsigned)V && v != u) {
+        sampled = true;
+        local = (u / W) == (v / W);
+      }
+    }
+  }
+  const unsigned ns = __popc(__ballot_sync(kFull, sampled));
+  const unsigned nl = __popc(__ballot_sync(kFull, local));
+  if ((threadIdx.x & 31) == 0 && ns) {
+    atomicAdd(out, (unsigned long long)nl);
+    atomicAdd(out + 1, (unsigned long long)ns);
+  }
 }
 
 // ----- validation (CC_FLAG_VALIDATE) -----
 
 template <typename OffT>
-__global__ void __launch_bounds__(256) k_validate_csr(const OffT* __restrict__ rp, const int* __restrict__ col, int V,
-                                                      OffT nnz, Ctl c) {
+__global__ void __launch_bounds__(kMaxBlock) k_validate_csr(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                            int V, OffT nnz, Ctl c) {
   const long long tid = global_tid(), nt = global_threads();
   if (tid == 0 && (rp[0] != 0 || rp[V] != nnz)) raise_error(c.st, kErrOutOfRange, kSiteValidate, -1);
   for (long long v = tid; v < V; v += nt)
@@ -86,17 +179,24 @@ __global__ void __launch_bounds__(256) k_validate_csr(const OffT* __restrict__ r
     if ((unsigned)col[a] >= (unsigned)V) raise_error(c.st, kErrOutOfRange, kSiteValidate, a);
 }
 
-__global__ void __launch_bounds__(256) k_validate_coo(const int* __restrict__ src, const int* __restrict__ dst, int V,
-                                                      long long E, Ctl c) {
+__global__ void __launch_bounds__(kMaxBlock) k_validate_coo(const int* __restrict__ src, const int* __restrict__ dst,
+                                                            int V, long long E, Ctl c) {
   for (long long i = global_tid(); i < E; i += global_threads())
     if ((unsigned)src[i] >= (unsigned)V || (unsigned)dst[i] >= (unsigned)V)
       raise_error(c.st, kErrOutOfRange, kSiteValidate, i);
 }
 
+// ----- host helpers -----
+
 template <typename F>
-int blocks_per_sm(F kernel, int block) {
+int blocks_per_sm(F kernel, int block, size_t smem) {
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -104,88 +204,119 @@ int blocks_per_sm(F kernel, int block) {
 }
 
 template <typename... Args>
-cudaError_t launch_coop(void (*kernel)(Args...), LaunchShape s, cudaStream_t stream, Args... args) {
+cudaError_t launch_kernel(void (*kernel)(Args...), LaunchShape s, size_t smem, bool coop, cudaStream_t stream,
+                          Args... args) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)s.grid);
   cfg.blockDim = dim3((unsigned)s.block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = coop ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Calls f(kernel) with the persistent CSR kernel variant (symmetric / hierarchical) of p.
+template <typename OffT, typename F>
+auto with_csr_persistent(const Problem& p, F&& f) {
+  const bool tiled = p.tile_w > 0;
+  if (p.sym) return tiled ? f(k_csr_persistent<OffT, true, true>) : f(k_csr_persistent<OffT, true, false>);
+  return tiled ? f(k_csr_persistent<OffT, false, true>) : f(k_csr_persistent<OffT, false, false>);
+}
+
+template <typename OffT, typename F>
+auto with_csr_hook(const Problem& p, F&& f) {
+  return p.sym ? f(k_hook_csr<OffT, true>) : f(k_hook_csr<OffT, false>);
 }
 
 }  // namespace
 
+size_t dynamic_smem_bytes(const Problem& p, int block) {
+  return (p.kind == kKindCsr && p.tile_w > 0) ? tiled_smem_bytes(p.tile_w, block) : 0;
+}
+
 int persistent_blocks_per_sm(const Problem& p, int block) {
-  if (p.kind == kKindCoo) return blocks_per_sm(k_coo_persistent, block);
-  if (p.rp64)
-    return p.sym ? blocks_per_sm(k_csr_persistent<long long, true>, block)
-                 : blocks_per_sm(k_csr_persistent<long long, false>, block);
-  return p.sym ? blocks_per_sm(k_csr_persistent<int, true>, block)
-               : blocks_per_sm(k_csr_persistent<int, false>, block);
+  const size_t smem = dynamic_smem_bytes(p, block);
+  if (p.kind == kKindCoo) return blocks_per_sm(k_coo_persistent, block, 0);
+  auto occ = [&](auto k) { return blocks_per_sm(k, block, smem); };
+  return p.rp64 ? with_csr_persistent<long long>(p, occ) : with_csr_persistent<int>(p, occ);
 }
 
 int stage_blocks_per_sm(const Problem& p, int block) {
-  if (p.kind == kKindCoo) return blocks_per_sm(k_hook_coo, block);
-  if (p.rp64)
-    return p.sym ? blocks_per_sm(k_hook_csr<long long, true>, block) : blocks_per_sm(k_hook_csr<long long, false>, block);
-  return p.sym ? blocks_per_sm(k_hook_csr<int, true>, block) : blocks_per_sm(k_hook_csr<int, false>, block);
+  if (p.kind == kKindCoo) return blocks_per_sm(k_hook_coo, block, 0);
+  auto occ = [&](auto k) { return blocks_per_sm(k, block, 0); };
+  return p.rp64 ? with_csr_hook<long long>(p, occ) : with_csr_hook<int>(p, occ);
 }
 
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
   if (p.kind == kKindCoo)
-    return launch_coop(k_coo_persistent, s, stream, p.src, p.dst, p.pi, p.V, p.m, p.segments, c);
+    return launch_kernel(k_coo_persistent, s, 0, true, stream, p.src, p.dst, p.pi, p.V, p.m, p.segments, c);
+  const size_t smem = dynamic_smem_bytes(p, s.block);
   if (p.rp64) {
     const long long* rp = static_cast<const long long*>(p.rp);
-    if (p.sym)
-      return launch_coop(k_csr_persistent<long long, true>, s, stream, rp, p.col, p.pi, p.V, p.m, p.segments, c);
-    return launch_coop(k_csr_persistent<long long, false>, s, stream, rp, p.col, p.pi, p.V, p.m, p.segments, c);
+    return with_csr_persistent<long long>(p, [&](auto k) {
+      return launch_kernel(k, s, smem, true, stream, rp, p.col, p.pi, p.V, (long long)p.m, p.segments, c);
+    });
   }
   const int* rp = static_cast<const int*>(p.rp);
-  const int nnz = (int)p.m;
-  if (p.sym) return launch_coop(k_csr_persistent<int, true>, s, stream, rp, p.col, p.pi, p.V, nnz, p.segments, c);
-  return launch_coop(k_csr_persistent<int, false>, s, stream, rp, p.col, p.pi, p.V, nnz, p.segments, c);
+  return with_csr_persistent<int>(p, [&](auto k) {
+    return launch_kernel(k, s, smem, true, stream, rp, p.col, p.pi, p.V, (int)p.m, p.segments, c);
+  });
 }
 
 cudaError_t launch_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream, int* launches) {
   int n = 0;
-  k_init<<<s.grid, s.block, 0, stream>>>(p.pi, p.V, c);
+  cudaError_t e = launch_kernel(k_init, s, 0, false, stream, p.pi, p.V, c);
+  if (e != cudaSuccess) return e;
   ++n;
+  const size_t smem = 0;  // the per-phase kernels use the plain hook
   for (int i = 0; i < p.segments; ++i) {
     if (p.kind == kKindCoo) {
-      k_hook_coo<<<s.grid, s.block, 0, stream>>>(p.src, p.dst, p.pi, p.V, split_point<long long>(p.m, p.segments, i),
-                                                 split_point<long long>(p.m, p.segments, i + 1), c);
+      e = launch_kernel(k_hook_coo, s, 0, false, stream, p.src, p.dst, p.pi, p.V,
+                        split_point<long long>(p.m, p.segments, i), split_point<long long>(p.m, p.segments, i + 1), c);
     } else if (p.rp64) {
       const long long* rp = static_cast<const long long*>(p.rp);
-      const long long a0 = split_point<long long>(p.m, p.segments, i), a1 = split_point<long long>(p.m, p.segments, i + 1);
-      if (p.sym) k_hook_csr<long long, true><<<s.grid, s.block, 0, stream>>>(rp, p.col, p.pi, p.V, a0, a1, c);
-      else k_hook_csr<long long, false><<<s.grid, s.block, 0, stream>>>(rp, p.col, p.pi, p.V, a0, a1, c);
+      const long long a0 = split_point<long long>(p.m, p.segments, i);
+      const long long a1 = split_point<long long>(p.m, p.segments, i + 1);
+      e = with_csr_hook<long long>(p, [&](auto k) { return launch_kernel(k, s, smem, false, stream, rp, p.col, p.pi, p.V, a0, a1, c); });
     } else {
       const int* rp = static_cast<const int*>(p.rp);
       const int a0 = split_point<int>((int)p.m, p.segments, i), a1 = split_point<int>((int)p.m, p.segments, i + 1);
-      if (p.sym) k_hook_csr<int, true><<<s.grid, s.block, 0, stream>>>(rp, p.col, p.pi, p.V, a0, a1, c);
-      else k_hook_csr<int, false><<<s.grid, s.block, 0, stream>>>(rp, p.col, p.pi, p.V, a0, a1, c);
+      e = with_csr_hook<int>(p, [&](auto k) { return launch_kernel(k, s, smem, false, stream, rp, p.col, p.pi, p.V, a0, a1, c); });
     }
-    k_jump<<<s.grid, s.block, 0, stream>>>(p.pi, p.V, c);
+    if (e != cudaSuccess) return e;
+    e = launch_kernel(k_jump, s, 0, false, stream, p.pi, p.V, c);
+    if (e != cudaSuccess) return e;
     n += 2;
   }
   *launches = n;
-  return cudaGetLastError();
+  return cudaSuccess;
+}
+
+cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* out, int threads, cudaStream_t stream) {
+  const LaunchShape s{(threads + 255) / 256, 256};
+  if (p.rp64)
+    return launch_kernel(k_sample_locality<long long>, s, 0, false, stream, static_cast<const long long*>(p.rp), p.col,
+                         p.V, (long long)p.m, W, out);
+  return launch_kernel(k_sample_locality<int>, s, 0, false, stream, static_cast<const int*>(p.rp), p.col, p.V, (int)p.m,
+                       W, out);
 }
 
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
-  if (p.kind == kKindCoo) {
-    k_validate_coo<<<s.grid, s.block, 0, stream>>>(p.src, p.dst, p.V, p.m, c);
-  } else if (p.rp64) {
-    k_validate_csr<long long><<<s.grid, s.block, 0, stream>>>(static_cast<const long long*>(p.rp), p.col, p.V, p.m, c);
-  } else {
-    k_validate_csr<int><<<s.grid, s.block, 0, stream>>>(static_cast<const int*>(p.rp), p.col, p.V, (int)p.m, c);
-  }
-  return cudaGetLastError();
+  if (p.kind == kKindCoo)
+    return launch_kernel(k_validate_coo, s, 0, false, stream, p.src, p.dst, p.V, p.m, c);
+  if (p.rp64)
+    return launch_kernel(k_validate_csr<long long>, s, 0, false, stream, static_cast<const long long*>(p.rp), p.col,
+                         p.V, (long long)p.m, c);
+  return launch_kernel(k_validate_csr<int>, s, 0, false, stream, static_cast<const int*>(p.rp), p.col, p.V, (int)p.m,
+                       c);
 }
 
 }  // namespace cc

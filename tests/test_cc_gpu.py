@@ -27,11 +27,15 @@ def dev():
     return torch.device("cuda:0")
 
 
+# hierarchical hook windows exercised by the tests: default (8192), off, smallest, largest
+TILES = [0, -1, 256, 32768]
+
+
 def gpu_csr(dev, row_ptr, col, *, mode="persistent", segments=0, sym=False, grid_blocks=0, block=256,
-            validate=False, expect_status=ccl.cc.CC_OK):
+            validate=False, expect_status=ccl.cc.CC_OK, tile=0, chunk=0):
     flags = ccl.CC_FLAG_SYNC | (ccl.CC_FLAG_SYMMETRIC if sym else 0) | (ccl.CC_FLAG_VALIDATE if validate else 0)
     with ccl.ConnectedComponents(0, mode=MODES[mode], segments=segments, flags=flags, grid_blocks=grid_blocks,
-                                 block=block) as cc:
+                                 block=block, tile_vertices=tile, chunk_arcs=chunk) as cc:
         rp = torch.from_numpy(np.ascontiguousarray(row_ptr)).to(dev)
         cl = torch.from_numpy(np.ascontiguousarray(col, np.int32)).to(dev)
         if expect_status != ccl.cc.CC_OK:
@@ -79,20 +83,28 @@ def union_of_all_small_graphs(max_n=5, seed=0):
                     src.append(base + a)
                     dst.append(base + b)
             base += n
+    if seed is None:
+        return base, np.array(src, np.int64), np.array(dst, np.int64)
     perm = np.random.default_rng(seed).permutation(base)
     return base, perm[np.array(src, np.int64)], perm[np.array(dst, np.int64)]
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("segments", [0, 1, 3, 64])
-def test_union_of_all_small_graphs(dev, mode, segments):
+@pytest.mark.parametrize("tile", TILES)
+def test_union_of_all_small_graphs(dev, mode, segments, tile):
     V, s, d = union_of_all_small_graphs()
     for sym in (False, True):
         rp, col = symmetric_csr(V, s, d, np.int32)
         want = expect(rp, col)
-        assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=segments, sym=sym), want, f"sym={sym}")
+        assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=segments, sym=sym, tile=tile), want, f"sym={sym}")
     rp, col = directed_csr(V, d, s, np.int64)  # one direction only, int64 offsets
-    assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=segments), expect(rp, col), "directed")
+    assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=segments, tile=tile), expect(rp, col), "directed")
+    # ordered (unshuffled) IDs keep most arcs inside one window
+    Vo, so, do_ = union_of_all_small_graphs(seed=None)
+    rp, col = symmetric_csr(Vo, so, do_, np.int32)
+    assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=segments, sym=True, tile=tile),
+                  expect(rp, col), "ordered")
     assert_labels(gpu_coo(dev, V, s, d, mode=mode, segments=segments), oracle.labels_uf_coo(V, s, d)[0], "coo")
 
 
@@ -106,6 +118,7 @@ def test_random_multigraphs_individually(dev, mode):
         rp, col = symmetric_csr(n, s, d, np.int32)
         want = expect(rp, col)
         assert_labels(gpu_csr(dev, rp, col, mode=mode, sym=True), want, "sym")
+        assert_labels(gpu_csr(dev, rp, col, mode=mode, sym=True, tile=-1), want, "sym plain hook")
         assert_labels(gpu_csr(dev, rp, col, mode=mode, segments=int(rng.integers(1, 9))), want, "segments")
         assert_labels(gpu_coo(dev, n, s, d, mode=mode), want, "coo")
 
@@ -152,17 +165,22 @@ def test_adversarial_shapes(dev, mode):
         want = expect(rp, col)
         for sym in (False, True):
             for segments in (1, 0, 7):
-                got = gpu_csr(dev, rp, col, mode=mode, sym=sym, segments=segments)
-                assert_labels(got, want, f"{name} sym={sym} s={segments}")
+                for tile in (0, -1, 1024):
+                    got = gpu_csr(dev, rp, col, mode=mode, sym=sym, segments=segments, tile=tile)
+                    assert_labels(got, want, f"{name} sym={sym} s={segments} tile={tile}")
 
 
 def test_launch_shapes(dev):
     g = gen.er_csr(50_000, 200_000, seed=41)
     want = expect(g.row_ptr, g.col)
-    for grid, block in ((1, 32), (1, 256), (3, 64), (7, 96), (152, 256), (0, 128)):
+    for grid, block in ((1, 32), (1, 256), (3, 64), (7, 96), (152, 256), (0, 128), (0, 512), (0, 1024), (5, 1024)):
         for mode in sorted(MODES):
-            got = gpu_csr(dev, g.row_ptr, g.col, mode=mode, grid_blocks=grid, block=block, sym=True)
-            assert_labels(got, want, f"grid={grid} block={block} {mode}")
+            for tile in (0, -1):
+                got = gpu_csr(dev, g.row_ptr, g.col, mode=mode, grid_blocks=grid, block=block, sym=True, tile=tile)
+                assert_labels(got, want, f"grid={grid} block={block} {mode} tile={tile}")
+    for chunk in (32, 1024):  # dynamically scheduled plain hook
+        got = gpu_csr(dev, g.row_ptr, g.col, sym=True, tile=-1, chunk=chunk)
+        assert_labels(got, want, f"chunk={chunk}")
 
 
 # ----------------------------------------------------------------------------------- workloads
@@ -174,8 +192,9 @@ def test_er_100k_1m(dev, mode):
     want = expect(g.row_ptr, g.col)
     for sym in (False, True):
         for segments in (0, 1, 5, 40):
-            assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=sym, segments=segments), want,
-                          f"sym={sym} s={segments}")
+            for tile in TILES:
+                assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=sym, segments=segments, tile=tile), want,
+                              f"sym={sym} s={segments} tile={tile}")
     rp64 = g.row_ptr.astype(np.int64)
     assert_labels(gpu_csr(dev, rp64, g.col, mode=mode, sym=True), want, "int64 offsets")
     src, dst = gen.er_coo(100_000, 1_000_000, seed=1)
@@ -195,23 +214,30 @@ def test_grid_4096_road(dev):
     want = expect(g.row_ptr, g.col)
     for mode in sorted(MODES):
         for sym in (True, False):
-            assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=sym), want, f"{mode} sym={sym}")
+            for tile in TILES:
+                for segments in (0, 1):
+                    assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=sym, tile=tile, segments=segments),
+                                  want, f"{mode} sym={sym} tile={tile} s={segments}")
 
 
 def test_grid_small_percolation(dev):
     for p in (0.3, 0.5, 0.7, 1.0):
         g = gen.grid_csr(700, p, seed=9)
         want = expect(g.row_ptr, g.col)
-        assert_labels(gpu_csr(dev, g.row_ptr, g.col, sym=True), want, f"p={p}")
+        for tile in TILES:
+            assert_labels(gpu_csr(dev, g.row_ptr, g.col, sym=True, tile=tile), want, f"p={p} tile={tile}")
 
 
 def test_rmat_mid(dev):
     g = gen.rmat_csr(20, 16, seed=1)
     want = expect(g.row_ptr, g.col)
     for mode in sorted(MODES):
-        assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=True), want, mode)
+        for tile in TILES:
+            assert_labels(gpu_csr(dev, g.row_ptr, g.col, mode=mode, sym=True, tile=tile), want, f"{mode} {tile}")
     g64 = gen.rmat_csr(18, 8, seed=2, offsets64=True)
-    assert_labels(gpu_csr(dev, g64.row_ptr, g64.col, sym=True), expect(g64.row_ptr, g64.col), "int64")
+    for tile in TILES:
+        assert_labels(gpu_csr(dev, g64.row_ptr, g64.col, sym=True, tile=tile), expect(g64.row_ptr, g64.col),
+                      f"int64 tile={tile}")
 
 
 def test_deterministic_repeats(dev):

@@ -8,9 +8,12 @@ HBM. Between steps L2 is flushed by writing a 256 MiB buffer (outside the timed 
 Prints ONE JSON line on rank 0.
 
 Workloads (seeded synthetic graphs, generated on the host before timing):
-  grid : road-like 4096 x 4096 lattice, each edge kept with p = 0.9, int32 CSR (default)
-  er   : Erdos-Renyi, V = 100,000, 1,000,000 drawn edges, int32 CSR
-  rmat : R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), permuted IDs, int64 offsets
+  grid    : road-like 4096 x 4096 lattice, each edge kept with p = 0.9, int32 CSR (default)
+  er      : Erdos-Renyi, V = 100,000, 1,000,000 drawn edges, int32 CSR
+  rmat    : R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), permuted IDs, int64 offsets
+  batched : 4096 independent graphs, |V| log-uniform in [1e3, 1e6], family uniform over
+            {ER avg degree 4..32, 2D grid p = 0.9, R-MAT edge factor 8}; one batched launch per step
+            (metric: graphs/s), with the single-graph kernel run graph by graph timed beside it
 """
 from __future__ import annotations
 
@@ -155,9 +158,46 @@ def cpu_oracle_rate(g, budget_s: float = 12.0, max_runs: int = 1000):
     return g.n_edges / statistics.mean(times), len(times), labels
 
 
+def run_reference_batched(args):
+    """The oracle on a bounded sample of the batch's graphs per step (graphs/s)."""
+    import oracle
+    specs = gen.batched_specs(args.n_graphs, seed=1)
+    rng = np.random.default_rng(5)
+    order = rng.permutation(len(specs))
+    graphs = [gen.make_graph(specs[g]) for g in order[:32]]
+
+    def step():
+        t1 = time.perf_counter()
+        n = 0
+        for h in graphs:
+            oracle.labels_uf_csr(h.row_ptr, h.col)
+            n += 1
+            if time.perf_counter() - t1 > 2.0:
+                break
+        return n, time.perf_counter() - t1
+
+    for _ in range(args.warmup):
+        step()
+    done = [step() for _ in range(args.steps)]
+    rate = sum(n for n, _ in done) / sum(t for _, t in done)
+    line = {
+        "impl": "reference", "metric": "batched graphs/sec", "value": rate, "unit": "graphs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(t for _, t in done),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batched%d" % args.n_graphs},
+        "cpu_baseline": {"value": rate, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": "up to 2 s per step of 32 randomly chosen graphs of the batch, union-find oracle"},
+        "e2e": {"value": rate, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    if args.workload == "batched":
+        return run_reference_batched(args)
     name, make = WORKLOADS[args.workload]
     g = make()
     import oracle
@@ -185,6 +225,203 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------- ours
+
+def device_uuid(torch, dev, local_rank):
+    gpu_id = str(local_rank)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        if "CUDA_VISIBLE_DEVICES" in os.environ:
+            gpu_id = os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]
+    return gpu_id
+
+
+def batch_bytes(b) -> int:
+    """Compulsory bytes of one batched labelling: every graph's arcs, row offsets and labels once,
+    plus the two offset tables."""
+    return 4 * b.total_arcs + 4 * (b.total_vertices + b.n_graphs) + 4 * b.total_vertices + 16 * (b.n_graphs + 1)
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import paper_1612_01178_gb300 as ccl
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.perf_counter()
+    b = gen.workload_batched(args.n_graphs, seed=1)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    flags = ccl.CC_FLAG_SYMMETRIC
+    cc = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, tile_vertices=args.tile,
+                                 segments=args.segments)
+    with torch.cuda.stream(stream):
+        v_off = torch.from_numpy(b.v_off).to(dev)
+        a_off = torch.from_numpy(b.a_off).to(dev)
+        rp = torch.from_numpy(b.row_ptr_cat).to(dev)
+        col = torch.from_numpy(b.col_cat).to(dev)
+        labels = torch.empty(b.total_vertices, dtype=torch.int32, device=dev)
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream.synchronize()
+    cc.batched(v_off, a_off, rp, col, labels)
+    cc.sync()
+    got = labels.cpu().numpy()
+    info = cc.run_info()
+    wl = cc.worklist()
+
+    # parity on sampled graphs (every kind represented) and the CPU baseline on a bounded sample
+    import oracle
+    rng = np.random.default_rng(5)
+    sample = sorted(set(rng.choice(b.n_graphs, size=min(64, b.n_graphs), replace=False).tolist()))
+    parity = "bit-exact on %d sampled graphs" % len(sample)
+    cpu_t, cpu_graphs, cpu_arcs = 0.0, 0, 0
+    for g in sample:
+        grp, gcol = b.graph(g)
+        t1 = time.perf_counter()
+        want, _ = oracle.labels_uf_csr(grp, gcol)
+        dt = time.perf_counter() - t1
+        if cpu_t < args.cpu_budget:
+            cpu_t += dt
+            cpu_graphs += 1
+            cpu_arcs += int(gcol.shape[0])
+        v0, v1 = int(b.v_off[g]), int(b.v_off[g + 1])
+        if not np.array_equal(got[v0:v1], want):
+            parity = "MISMATCH in graph %d" % g
+            break
+
+    def timed(fn, steps):
+        ts = []
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(z) for a, z in ts]
+
+    def batched_step():
+        cc.batched(v_off, a_off, rp, col, labels)
+
+    timed(batched_step, args.warmup)
+    cc.sync()
+    sampler = ClockSampler(device_uuid(torch, dev, local_rank))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    step_ms = timed(batched_step, args.steps)
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    cc.sync()
+    ms = statistics.mean(step_ms)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+
+    # the same single-graph kernel run graph by graph (best per-graph hook choice, no sampling)
+    rp_slices, col_slices, lab_slices, ctxs = [], [], [], {}
+    for kind in ("plain", "tiled"):
+        ctxs[kind] = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags,
+                                             tile_vertices=-1 if kind == "plain" else 32768)
+    for g in range(b.n_graphs):
+        v0, v1, a0, a1 = int(b.v_off[g]), int(b.v_off[g + 1]), int(b.a_off[g]), int(b.a_off[g + 1])
+        rp_slices.append(rp[v0 + g: v1 + g + 1])
+        col_slices.append(col[a0:a1])
+        lab_slices.append(labels[v0:v1])
+
+    def by_graph_step():
+        for g in range(b.n_graphs):
+            c2 = ctxs["tiled" if b.kinds[g] == "grid" else "plain"]
+            c2.csr(rp_slices[g], col_slices[g], lab_slices[g])
+
+    timed(by_graph_step, 1)
+    bg_ms = statistics.mean(timed(by_graph_step, max(1, min(args.steps, 3))))
+    for c2 in ctxs.values():
+        c2.sync()
+    bg_ok = np.array_equal(labels.cpu().numpy(), got)
+    for c2 in ctxs.values():
+        c2.close()
+
+    # end to end: pinned host inputs copied in, batched call, labels copied out
+    e2e = None
+    if not args.no_e2e:
+        h_v = torch.from_numpy(b.v_off).pin_memory()
+        h_a = torch.from_numpy(b.a_off).pin_memory()
+        h_rp = torch.from_numpy(b.row_ptr_cat).pin_memory()
+        h_col = torch.from_numpy(b.col_cat).pin_memory()
+        h_out = torch.empty(b.total_vertices, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                v_off.copy_(h_v, non_blocking=True)
+                a_off.copy_(h_a, non_blocking=True)
+                rp.copy_(h_rp, non_blocking=True)
+                col.copy_(h_col, non_blocking=True)
+            cc.batched(v_off, a_off, rp, col, labels)
+            with torch.cuda.stream(stream):
+                h_out.copy_(labels, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        tt = []
+        for _ in range(3):
+            t1 = time.perf_counter()
+            e2e_step()
+            tt.append(time.perf_counter() - t1)
+        cc.sync()
+        e2e_s = statistics.mean(tt)
+        e2e = {"value": world * b.n_graphs / e2e_s, "unit": "graphs/s",
+               "h2d_bytes_per_step": int(h_v.nbytes + h_a.nbytes + h_rp.nbytes + h_col.nbytes),
+               "d2h_bytes_per_step": int(h_out.nbytes), "ms_per_step": 1000 * e2e_s,
+               "labels_match": bool(np.array_equal(h_out.numpy(), got))}
+
+    if rank != 0:
+        cc.close()
+        return 0
+    peak, peak_kind = measured_peaks()
+    b_alg = batch_bytes(b)
+    achieved = b_alg / (ms / 1000) / 1e9
+    kinds = {k: b.kinds.count(k) for k in sorted(set(b.kinds))}
+    line = {
+        "metric": "batched graphs/sec", "value": world * b.n_graphs / (ms_max / 1000), "unit": "graphs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batched%d" % b.n_graphs, "n_graphs": b.n_graphs, "total_vertices": b.total_vertices,
+                   "total_arcs": b.total_arcs, "kinds": kinds, "seed": 1, "flags": "CC_FLAG_SYMMETRIC",
+                   "window": info["tile_vertices"], "block": info["block"], "grid_blocks": info["grid_blocks"],
+                   "worklist": {"pairs": wl[0], "segments": wl[1]},
+                   "l2": "inputs larger than L2; 256 MiB flush between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "generation_s": round(gen_s, 1)},
+        "edges_per_s": world * (b.total_arcs // 2) / (ms_max / 1000),
+        "graph_by_graph": {"value": b.n_graphs / (bg_ms / 1000), "unit": "graphs/s", "ms_per_step": bg_ms,
+                           "launches_per_step": b.n_graphs, "labels_match": bool(bg_ok),
+                           "speedup_of_batched": bg_ms / ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind, "bytes_alg_per_launch": b_alg,
+                     "kernel": "k_batched<SYM>", "kernel_ms_mean": ms},
+        "cpu_baseline": {"value": cpu_graphs / cpu_t if cpu_t else None, "unit": "graphs/s", "cores": 1,
+                         "kind": "oracle", "edges_per_s": (cpu_arcs // 2) / cpu_t if cpu_t else None,
+                         "sample": f"{cpu_graphs} sampled graphs of the batch ({cpu_arcs} arcs), union-find oracle, "
+                                   "1 host thread"},
+        "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps, "parity": parity,
+    }
+    print(json.dumps(line), flush=True)
+    cc.close()
+    return 0 if parity.startswith("bit-exact") and bg_ok else 3
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -364,7 +601,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="grid")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="grid")
+    ap.add_argument("--n-graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--mode", choices=["persistent", "multi"], default="persistent")
     ap.add_argument("--segments", type=int, default=0, help="0 = the average degree (Section III-B)")
     ap.add_argument("--tile", type=int, default=0, help="hook window: 0 = automatic, -1 = plain hook")
@@ -379,16 +617,17 @@ def main(argv=None):
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    run = run_batched if args.workload == "batched" else run_ours
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
         try:
-            return run_ours(args, rank, world, local_rank)
+            return run(args, rank, world, local_rank)
         finally:
             dist.destroy_process_group()
-    return run_ours(args, rank, world, local_rank)
+    return run(args, rank, world, local_rank)
 
 
 if __name__ == "__main__":

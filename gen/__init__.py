@@ -199,3 +199,101 @@ def workload_rmat_26(seed: int = 1) -> CSR:
 
 def loguniform_int(rng: np.random.Generator, lo: float, hi: float) -> int:
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+# ----------------------------------------------------------------------------------------------
+# Batches of independent graphs over a graph-offset table.
+
+class Batch:
+    """Concatenated CSR of independent graphs.
+
+    Graph g owns vertices [v_off[g], v_off[g+1]) of the concatenated label array, arcs
+    [a_off[g], a_off[g+1]) of col_cat (graph-local IDs), and its V_g + 1 graph-local row offsets
+    start at row_ptr_cat[v_off[g] + g]."""
+
+    __slots__ = ("v_off", "a_off", "row_ptr_cat", "col_cat", "kinds")
+
+    def __init__(self, v_off, a_off, row_ptr_cat, col_cat, kinds):
+        self.v_off, self.a_off, self.row_ptr_cat, self.col_cat, self.kinds = v_off, a_off, row_ptr_cat, col_cat, kinds
+
+    @property
+    def n_graphs(self) -> int:
+        return int(self.v_off.shape[0] - 1)
+
+    @property
+    def total_vertices(self) -> int:
+        return int(self.v_off[-1])
+
+    @property
+    def total_arcs(self) -> int:
+        return int(self.a_off[-1])
+
+    def graph(self, g: int):
+        """(row_ptr, col) views of graph g (graph-local IDs)."""
+        v0, v1 = int(self.v_off[g]), int(self.v_off[g + 1])
+        a0, a1 = int(self.a_off[g]), int(self.a_off[g + 1])
+        return self.row_ptr_cat[v0 + g: v1 + g + 1], self.col_cat[a0:a1]
+
+    def __repr__(self):
+        return f"Batch(n={self.n_graphs}, V={self.total_vertices}, arcs={self.total_arcs})"
+
+
+def batch_from_graphs(graphs, kinds=None) -> Batch:
+    """Concatenate CSR graphs (int32 row offsets) into a Batch."""
+    n = len(graphs)
+    v_off = np.zeros(n + 1, np.int64)
+    a_off = np.zeros(n + 1, np.int64)
+    for g, h in enumerate(graphs):
+        v_off[g + 1] = v_off[g] + h.n_vertices
+        a_off[g + 1] = a_off[g] + h.nnz
+    row_ptr_cat = np.empty(int(v_off[-1]) + n, np.int32)
+    col_cat = np.empty(int(a_off[-1]), np.int32)
+    for g, h in enumerate(graphs):
+        v0 = int(v_off[g]) + g
+        row_ptr_cat[v0: v0 + h.n_vertices + 1] = h.row_ptr
+        col_cat[int(a_off[g]): int(a_off[g + 1])] = h.col
+    return Batch(v_off, a_off, row_ptr_cat, col_cat, kinds or [h.name for h in graphs])
+
+
+def mixed_spec(kind: str, v_target: int, seed: int, rng: np.random.Generator) -> dict:
+    """Parameters of one graph of the batched/served mixes, sized for about v_target vertices:
+    'er'   Erdos-Renyi, average degree d ~ U{4..32} (E = d V / 2 drawn edges);
+    'grid' square 2D grid, side round(sqrt(V)), p = 0.9;
+    'rmat' R-MAT, scale round(log2 V), edge factor 8."""
+    if kind == "er":
+        d = int(rng.integers(4, 33))
+        V = max(1, v_target)
+        return dict(kind="er", n_vertices=V, n_edges=d * V // 2, seed=seed)
+    if kind == "grid":
+        return dict(kind="grid", side=max(1, int(round(math.sqrt(v_target)))), p=0.9, seed=seed)
+    if kind == "rmat":
+        return dict(kind="rmat", scale=max(1, int(round(math.log2(max(2, v_target))))), edge_factor=8, seed=seed)
+    raise ValueError(kind)
+
+
+def make_graph(spec: dict) -> CSR:
+    if spec["kind"] == "er":
+        return er_csr(spec["n_vertices"], spec["n_edges"], spec["seed"])
+    if spec["kind"] == "grid":
+        return grid_csr(spec["side"], spec["p"], spec["seed"])
+    return rmat_csr(spec["scale"], spec["edge_factor"], spec["seed"])
+
+
+def batched_specs(n_graphs: int = 4096, seed: int = 1, vmin: float = 1e3, vmax: float = 1e6,
+                  kinds=("er", "grid", "rmat")) -> list:
+    """Specs of the batched workload: |V| log-uniform in [vmin, vmax], family drawn uniformly per
+    graph from `kinds`; graph g is generated with seed 1000 + g."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for g in range(n_graphs):
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        v_target = loguniform_int(rng, vmin, vmax)
+        specs.append(mixed_spec(kind, v_target, 1000 + g, rng))
+    return specs
+
+
+def workload_batched(n_graphs: int = 4096, seed: int = 1, vmin: float = 1e3, vmax: float = 1e6,
+                     kinds=("er", "grid", "rmat")) -> Batch:
+    """The batched workload as one Batch (see batched_specs)."""
+    specs = batched_specs(n_graphs, seed, vmin, vmax, kinds)
+    return batch_from_graphs([make_graph(s) for s in specs], [s["kind"] for s in specs])

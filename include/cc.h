@@ -142,6 +142,29 @@ cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const v
 cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const int32_t* src,
                         const int32_t* dst, int32_t* labels);
 
+/* Connected components of a batch of independent graphs in one persistent launch
+ * (the paper has one graph per call; batching is this library's addition). Graph g has
+ * V_g = v_off[g+1] - v_off[g] vertices and n_g = a_off[g+1] - a_off[g] arcs:
+ *   v_off, a_off     device int64 [n_graphs + 1], non-decreasing, v_off[0] = a_off[0] = 0,
+ *                    v_off[n_graphs] = total_vertices, a_off[n_graphs] = total_arcs.
+ *   row_ptr_cat      device int32; graph g's row offsets (graph-local arc indices, V_g + 1
+ *                    of them) start at row_ptr_cat + v_off[g] + g (total_vertices + n_graphs
+ *                    entries in all).
+ *   col_idx_cat      device int32 [total_arcs]; graph g's arcs at a_off[g] .. a_off[g+1],
+ *                    graph-local vertex IDs in [0, V_g).
+ *   labels_cat       device int32 [total_vertices], output: graph g's labels at v_off[g],
+ *                    graph-local minimum vertex IDs.
+ *   graph_status     device int32 [n_graphs] or NULL: set to CC_OK, or to
+ *                    CC_ERR_OUT_OF_RANGE for a graph with an endpoint outside [0, V_g).
+ * total_vertices must be below 2^31 (labels are computed with batch-global IDs); each graph
+ * must have fewer than 2^31 arcs. Graphs of at most tile_vertices vertices (default 32768)
+ * are labelled inside one CTA's shared memory; larger graphs go through the two-phase hook
+ * with a locality sample per window (tile_vertices = -1: their windows are hooked arc by arc).
+ * CC_FLAG_SYMMETRIC, CC_FLAG_SYNC and CC_FLAG_PHASE_TIMES apply as for cc_labels_csr. */
+cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertices, int64_t total_arcs,
+                            const int64_t* v_off, const int64_t* a_off, const int32_t* row_ptr_cat,
+                            const int32_t* col_idx_cat, int32_t* labels_cat, int32_t* graph_status);
+
 /* cc_labels_csr with HOST buffers: copies row_ptr and col_idx from host memory
    (pinned memory gives full copy bandwidth) into context-owned device buffers,
    runs the method, copies the labels back into the host array `labels`, and

@@ -90,6 +90,7 @@ SIGNATURES = {
     "cc_labels_csr": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
     "cc_labels_coo": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "cc_labels_csr_host": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
+    "cc_labels_batched": (ctypes.c_int, [_vp, _i32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cc_sync": (ctypes.c_int, [_vp]),
     "cc_last_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(cc_run_info)]),
     "cc_last_error_message": (ctypes.c_char_p, [_vp]),
@@ -263,6 +264,36 @@ def cc_labels_coo(ctx, n_vertices: int, src, dst, labels=None):
     return labels
 
 
+def cc_labels_batched(ctx, v_off, a_off, row_ptr_cat, col_idx_cat, labels=None, graph_status=None):
+    """Labels of a batch of graphs given as CUDA tensors: int64 offset tables v_off/a_off
+    [n_graphs+1], per-graph int32 row offsets concatenated (graph g's at v_off[g] + g), int32
+    col_idx concatenated. Returns the int32 labels tensor (graph-local minimum IDs)."""
+    import torch
+    _dev_tensor(v_off, torch.int64, "v_off")
+    _dev_tensor(a_off, torch.int64, "a_off")
+    _dev_tensor(row_ptr_cat, torch.int32, "row_ptr_cat")
+    _dev_tensor(col_idx_cat, torch.int32, "col_idx_cat")
+    n = v_off.numel() - 1
+    if n < 0 or a_off.numel() != n + 1:
+        raise ValueError("v_off and a_off must both hold n_graphs + 1 offsets")
+    total_v = row_ptr_cat.numel() - n
+    if labels is None:
+        labels = torch.empty(max(total_v, 0), dtype=torch.int32, device=v_off.device)
+    _dev_tensor(labels, torch.int32, "labels")
+    if labels.numel() != total_v:
+        raise ValueError("labels must hold total_vertices entries (row_ptr_cat has total_vertices + n_graphs)")
+    if graph_status is not None:
+        _dev_tensor(graph_status, torch.int32, "graph_status")
+        if graph_status.numel() != n:
+            raise ValueError("graph_status must hold n_graphs entries")
+    st = load().cc_labels_batched(ctx, n, total_v, col_idx_cat.numel(), v_off.data_ptr(), a_off.data_ptr(),
+                                  row_ptr_cat.data_ptr(), col_idx_cat.data_ptr() if col_idx_cat.numel() else None,
+                                  labels.data_ptr() if total_v else None,
+                                  graph_status.data_ptr() if graph_status is not None else None)
+    _check(st, "cc_labels_batched", ctx)
+    return labels
+
+
 def cc_labels_csr_host(ctx, row_ptr: np.ndarray, col_idx: np.ndarray, labels: np.ndarray | None = None):
     """cc_labels_csr on host (numpy) arrays; synchronous. Pinned arrays copy fastest."""
     rp = row_ptr
@@ -341,6 +372,9 @@ class ConnectedComponents:
 
     def coo(self, n_vertices, src, dst, labels=None):
         return cc_labels_coo(self._ctx, n_vertices, src, dst, labels)
+
+    def batched(self, v_off, a_off, row_ptr_cat, col_idx_cat, labels=None, graph_status=None):
+        return cc_labels_batched(self._ctx, v_off, a_off, row_ptr_cat, col_idx_cat, labels, graph_status)
 
     def csr_host(self, row_ptr, col_idx, labels=None):
         return cc_labels_csr_host(self._ctx, row_ptr, col_idx, labels)

@@ -28,6 +28,8 @@ struct cc_ctx {
   size_t d_wl_pairs = 0;
   int* d_ovf = nullptr;
   size_t d_ovf_n = 0;
+  long long* d_unit_start = nullptr;  // batched: first window of each graph
+  size_t d_unit_start_n = 0;
   // automatic hook choice: locality sample buffer and the last decision
   unsigned long long* d_sample = nullptr;
   unsigned long long* h_sample = nullptr;
@@ -436,6 +438,101 @@ cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const 
   return st;
 }
 
+cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertices, int64_t total_arcs,
+                            const int64_t* v_off, const int64_t* a_off, const int32_t* row_ptr_cat,
+                            const int32_t* col_idx_cat, int32_t* labels_cat, int32_t* graph_status) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_graphs < 0 || total_vertices < 0 || total_vertices >= INT32_MAX || total_arcs < 0) return CC_ERR_INVALID_ARG;
+  if (n_graphs > 0 && (!v_off || !a_off || !row_ptr_cat)) return CC_ERR_INVALID_ARG;
+  if (total_vertices > 0 && !labels_cat) return CC_ERR_INVALID_ARG;
+  if (total_arcs > 0 && (!col_idx_cat || total_vertices == 0)) return CC_ERR_INVALID_ARG;
+  if (overlaps(labels_cat, (size_t)total_vertices * 4, col_idx_cat, (size_t)total_arcs * 4) ||
+      overlaps(labels_cat, (size_t)total_vertices * 4, row_ptr_cat, (size_t)(total_vertices + n_graphs) * 4))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  const cc_options& o = ctx->opt;
+  if (n_graphs == 0) return (o.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+
+  const int W = o.tile_vertices > 0 ? window_for(INT32_MAX, o.tile_vertices) : kDefaultTileVertices;
+  int block = o.block > 0 ? o.block : kTiledBlock;
+  const bool sym = (o.flags & CC_FLAG_SYMMETRIC) != 0;
+  int per_sm = cc::batched_blocks_per_sm(sym, block, W);
+  while (per_sm <= 0 && block > 32) {
+    block /= 2;
+    per_sm = cc::batched_blocks_per_sm(sym, block, W);
+  }
+  if (per_sm <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "batched occupancy");
+  long long grid = (long long)per_sm * ctx->num_sms;
+  if (o.grid_blocks > 0) grid = std::min<long long>(grid, o.grid_blocks);
+
+  // Scratch: window table, worklist (one pair per vertex, at least 2^20, at most one per arc),
+  // and the list of windows hooked arc by arc (at most one entry per window).
+  const size_t n_windows = (size_t)(total_vertices / W) + (size_t)n_graphs + 1;
+  const size_t cap = (size_t)std::max<long long>(1, std::min<long long>(std::max<long long>(total_arcs, 1),
+                                                                        std::max<long long>(total_vertices, 1 << 20)));
+  if (grow_buffer(&ctx->d_unit_start, &ctx->d_unit_start_n, (size_t)n_graphs + 1) != cudaSuccess ||
+      grow_buffer(&ctx->d_wl, &ctx->d_wl_pairs, cap) != cudaSuccess ||
+      grow_buffer(&ctx->d_ovf, &ctx->d_ovf_n, n_windows) != cudaSuccess) {
+    std::snprintf(ctx->last_error, sizeof(ctx->last_error), "batched scratch allocation failed");
+    return CC_ERR_OOM;
+  }
+  cc::Ctl c;
+  c.st = ctx->d_status;
+  c.timeout_ns = o.timeout_ns;
+  c.tile_w = W;
+  c.wl = ctx->d_wl;
+  c.wl_cap = ctx->d_wl_pairs;
+  c.segments_b = o.segments;
+  c.window_mode = o.tile_vertices == -1 ? cc::kWindowsPlain : cc::kWindowsSampled;
+  c.skip_arrival_block = ctx->skip_arrival_block;
+  ctx->skip_arrival_block = -1;
+
+  cc::BatchProblem p{};
+  p.n_graphs = n_graphs;
+  p.v_off = reinterpret_cast<const long long*>(v_off);
+  p.a_off = reinterpret_cast<const long long*>(a_off);
+  p.rp_cat = row_ptr_cat;
+  p.col_cat = col_idx_cat;
+  p.labels = labels_cat;
+  p.graph_status = graph_status;
+  p.unit_start = ctx->d_unit_start;
+  p.plain_units = ctx->d_ovf;
+  p.plain_cap = (int)std::min<size_t>(ctx->d_ovf_n, INT32_MAX);
+  p.total_v = total_vertices;
+  p.sym = sym;
+
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
+  if (e == cudaSuccess && graph_status) e = cudaMemsetAsync(graph_status, 0, sizeof(int32_t) * n_graphs, ctx->stream);
+  if (e == cudaSuccess && (o.flags & CC_FLAG_PHASE_TIMES)) {
+    if (!ctx->d_phase && cudaMalloc(&ctx->d_phase, kPhaseSlots * sizeof(unsigned long long)) != cudaSuccess) {
+      ctx->d_phase = nullptr;
+      cudaGetLastError();
+      return CC_ERR_OOM;
+    }
+    e = cudaMemsetAsync(ctx->d_phase, 0, kPhaseSlots * sizeof(unsigned long long), ctx->stream);
+    c.phase_ns = ctx->d_phase;
+    c.phase_cap = kPhaseSlots;
+    ctx->phase_valid = true;
+  } else {
+    ctx->phase_valid = false;
+  }
+  if (e == cudaSuccess) e = cc::launch_batched(p, c, cc::LaunchShape{(int)grid, block}, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batched launch");
+  cc_run_info info{};
+  info.mode = CC_MODE_PERSISTENT;
+  info.segments = o.segments;
+  info.grid_blocks = (int)grid;
+  info.block = block;
+  info.launches = 1;
+  info.tile_vertices = W;
+  info.worklist_capacity = (int64_t)ctx->d_wl_pairs;
+  ctx->last = info;
+  if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
+  return CC_OK;
+}
+
 static cc_status grow(cc_ctx* ctx, void** buf, size_t* have, size_t need) {
   if (need <= *have) return CC_OK;
   if (*buf) cudaFree(*buf);
@@ -557,6 +654,7 @@ void cc_destroy(cc_ctx* ctx) {
     if (ctx->d_phase) cudaFree(ctx->d_phase);
     if (ctx->d_wl) cudaFree(ctx->d_wl);
     if (ctx->d_ovf) cudaFree(ctx->d_ovf);
+    if (ctx->d_unit_start) cudaFree(ctx->d_unit_start);
     if (ctx->d_sample) cudaFree(ctx->d_sample);
     if (ctx->h_sample) cudaFreeHost(ctx->h_sample);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -1,0 +1,351 @@
+// Batched connected components: thousands of graphs of uneven size in one persistent launch.
+//
+// The batch is the disjoint union of its graphs over a graph-offset table: graph g owns the
+// vertex range [v_off[g], v_off[g+1]) of the concatenated label array and the arc range
+// [a_off[g], a_off[g+1]) of the concatenated col_idx; its row offsets (graph-local, V_g + 1 of
+// them) start at row_ptr_cat + v_off[g] + g. Each graph is cut into windows of W vertices; a
+// window is the unit of work of phase A.
+//
+//  - A graph of one window (V_g <= W) is labelled completely inside one CTA: every arc is hooked
+//    on the shared-memory parent array and the compressed labels (graph-local minimum IDs) are
+//    written once. No global atomics and no second pass.
+//  - A larger graph is labelled on the concatenated array with global IDs (v_off[g] + local):
+//    a window whose sampled arcs mostly stay inside it runs phase A of the two-phase hook (local
+//    hooks, stars written, other arcs to the worklist); a window without that locality only
+//    writes pi(x) = x and is hooked arc by arc in phase B. Phase B hooks the worklist and those
+//    windows on pi in s' = 2|E'|/|V| segments, each followed by a Multi-Jump over the vertices of
+//    the multi-window graphs; a last pass turns their global IDs into graph-local ones.
+//
+// Every write to pi is a CAS on a root towards a smaller vertex of the same graph (IDs of
+// different graphs never meet: an arc only joins vertices of its own graph), so the argument of
+// the single-graph kernels gives, per graph, the graph-local minimum vertex ID of each component.
+#include "cc_internal.h"
+
+namespace cc {
+
+namespace {
+
+constexpr int kMaxBlockB = 1024;
+
+struct Batch {
+  int n_graphs;
+  const long long* v_off;
+  const long long* a_off;
+  const int* rp_cat;
+  const int* col_cat;
+  int* labels;
+  int* graph_status;       // nullable: per-graph error code
+  long long* unit_start;   // [n_graphs + 1] first window of each graph (filled by the kernel)
+  int* plain_units;        // windows hooked arc by arc in phase B
+  int plain_cap;
+  int total_v;
+};
+
+__device__ __forceinline__ long long units_of(long long vg, int W) { return vg <= 0 ? 0 : (vg + W - 1) / W; }
+
+// Block-wide inclusive scan of one value per thread (blockDim.x a multiple of 32).
+__device__ __forceinline__ long long block_scan(long long x, long long* warp_sums, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(kFull, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = lane < nwarps ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(kFull, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nwarps) warp_sums[lane] = w;
+    if (lane == nwarps - 1) *total = w;
+  }
+  __syncthreads();
+  const long long r = x + (warp > 0 ? warp_sums[warp - 1] : 0);
+  __syncthreads();
+  return r;
+}
+
+// Graph owning window u: largest g with unit_start[g] <= u (graphs without vertices own none).
+__device__ __forceinline__ int graph_of_unit(const long long* unit_start, int n, long long u) {
+  int lo = 0, hi = n;  // unit_start[lo] <= u < unit_start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (unit_start[mid] <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+struct UnitInfo {
+  int g, w0, nrows, vbase, vg;
+  bool single;
+  long long nnz;
+  const int* rp;
+  const int* col;
+};
+
+__device__ __forceinline__ UnitInfo unit_info(const Batch& b, long long u, int W) {
+  UnitInfo ui;
+  ui.g = graph_of_unit(b.unit_start, b.n_graphs, u);
+  const long long vo = b.v_off[ui.g];
+  ui.vg = (int)(b.v_off[ui.g + 1] - vo);
+  ui.vbase = (int)vo;
+  const long long k = u - b.unit_start[ui.g];
+  ui.single = (b.unit_start[ui.g + 1] - b.unit_start[ui.g]) == 1;
+  ui.w0 = (int)(k * W);
+  ui.nrows = (ui.vg - ui.w0) < W ? (ui.vg - ui.w0) : W;
+  const long long ao = b.a_off[ui.g];
+  ui.nnz = b.a_off[ui.g + 1] - ao;
+  ui.rp = b.rp_cat + vo + ui.g;
+  ui.col = b.col_cat + ao;
+  return ui;
+}
+
+// Fraction test of one window's locality by warp 0: the middle arc of 32 rows spread over the
+// window; true when at least half of the sampled arcs stay in the window.
+__device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
+  const int lane = threadIdx.x & 31;
+  const int r = ui.w0 + (int)(((long long)lane * ui.nrows) / 32);
+  bool sampled = false, local = false;
+  const int a0 = ui.rp[r], a1 = ui.rp[r + 1];
+  if (a0 >= 0 && a0 < a1 && (long long)a1 <= ui.nnz) {
+    const int v = ui.col[a0 + (a1 - a0) / 2];
+    if ((unsigned)v < (unsigned)ui.vg && v != r) {
+      sampled = true;
+      local = (unsigned)(v - ui.w0) < (unsigned)ui.nrows;
+    }
+  }
+  const int ns = __popc(__ballot_sync(kFull, sampled));
+  const int nl = __popc(__ballot_sync(kFull, local));
+  return 2 * nl >= ns;
+}
+
+template <bool SYM>
+__device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ctl& c) {
+  __shared__ long long s_warp_sums[32];
+  __shared__ long long s_total;
+  __shared__ unsigned long long s_unit;
+  __shared__ int s_ovf, s_bad, s_plain;
+  if (ld_relaxed(&c.st->error) != 0) return;
+  unsigned epoch = 0;
+  const int W = c.tile_w;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+
+  // Windows per graph -> unit_start (block 0).
+  if (blockIdx.x == 0) {
+    long long carry = 0;
+    if (threadIdx.x == 0) b.unit_start[0] = 0;
+    for (int base = 0; base < b.n_graphs; base += blockDim.x) {
+      const int g = base + threadIdx.x;
+      const long long n = g < b.n_graphs ? units_of(b.v_off[g + 1] - b.v_off[g], W) : 0;
+      const long long incl = block_scan(n, s_warp_sums, &s_total);
+      if (g < b.n_graphs) b.unit_start[g + 1] = carry + incl;
+      carry += s_total;
+    }
+  }
+  if (!grid_sync(c, epoch)) return;
+  const long long n_units = *reinterpret_cast<volatile long long*>(b.unit_start + b.n_graphs);
+
+  // Phase A over all windows of all graphs.
+  int* lp = smem;
+  WarpSink sink;
+  sink.buf = reinterpret_cast<int2*>(smem + W) + (threadIdx.x >> 5) * kSinkPairs;
+  sink.count = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = atomicAdd(&c.st->counters[0], 1ull);
+      s_ovf = 0;
+      s_bad = 0;
+    }
+    __syncthreads();
+    const unsigned long long k = s_unit;
+    if (k >= (unsigned long long)n_units) break;
+    const UnitInfo ui = unit_info(b, (long long)k, W);
+    for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) lp[i] = i;
+    if (threadIdx.x < 32) {  // warp 0 decides how the window is hooked
+      bool local = true;
+      if (!ui.single) local = c.window_mode == kWindowsPlain ? false : window_is_local(ui);
+      if (ui.nnz > 0x7fffffffLL) {  // graph too large for int32 row offsets: reported, not hooked
+        local = true;
+        if (threadIdx.x == 0) {
+          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          s_bad = 1;
+        }
+      }
+      if (threadIdx.x == 0) s_plain = !local;
+    }
+    __syncthreads();
+    if (s_plain) {
+      for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[ui.vbase + ui.w0 + i] = ui.vbase + ui.w0 + i;
+      if (threadIdx.x == 0) {
+        const unsigned long long j = atomicAdd(&c.st->counters[3], 1ull);
+        if (j < (unsigned long long)b.plain_cap) b.plain_units[j] = (int)k;
+        else raise_error(c.st, kErrInternal, kSiteHookGuard, (long long)k);  // capacity is the window count
+      }
+    } else {
+      if (ui.nnz <= 0x7fffffffLL)
+        phase_a_window<int, SYM>(ui.rp, ui.col, ui.vg, (int)ui.nnz, ui.w0, ui.nrows, ui.vbase, lp, sink, &s_ovf,
+                                 &s_bad, c);
+      else
+        __syncthreads();
+      volatile int* vlp = lp;
+      if (ui.single) {
+        for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[ui.vbase + i] = lfind(vlp, i);
+      } else {
+        const int base = ui.vbase + ui.w0;
+        for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[base + i] = base + lfind(vlp, i);
+      }
+      if (threadIdx.x == 0 && s_ovf) {  // worklist full: hook this window arc by arc in phase B
+        const unsigned long long j = atomicAdd(&c.st->counters[3], 1ull);
+        if (j < (unsigned long long)b.plain_cap) b.plain_units[j] = (int)k;
+      }
+    }
+    if (threadIdx.x == 0 && s_bad && b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+    __syncthreads();
+  }
+  if (!grid_sync(c, epoch)) return;
+
+  const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&c.st->counters[2]);
+  const unsigned long long n_pairs = cur < c.wl_cap ? cur : c.wl_cap;
+  unsigned long long n_plain = *reinterpret_cast<volatile unsigned long long*>(&c.st->counters[3]);
+  n_plain = n_plain < (unsigned long long)b.plain_cap ? n_plain : (unsigned long long)b.plain_cap;
+  long long s2 = c.segments_b > 0 ? c.segments_b : (long long)((2.0 * (double)n_pairs) / (double)b.total_v + 0.5);
+  s2 = s2 < 1 ? 1 : (s2 > 4096 ? 4096 : s2);
+  if (n_pairs == 0 && n_plain == 0) s2 = 0;  // every tree is already a star: only the relabelling is left
+  if (tid == 0) {
+    c.st->report[0] = n_pairs;
+    c.st->report[1] = (unsigned long long)s2;
+  }
+  constexpr int K = kPairK;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (long long seg = 0; seg < s2; ++seg) {
+    const unsigned long long p0 = split_point<unsigned long long>(n_pairs, s2, seg);
+    const unsigned long long p1 = split_point<unsigned long long>(n_pairs, s2, seg + 1);
+    const unsigned long long T = (unsigned long long)nt;
+    for (unsigned long long base = p0 + (unsigned long long)tid; base < p1; base += T * K) {
+      int u[K], v[K];
+      bool live[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const unsigned long long i = base + (unsigned long long)j * T;
+        live[j] = i < p1;
+        const int2 e = live[j] ? c.wl[i] : make_int2(0, 0);
+        u[j] = e.x;
+        v[j] = e.y;
+      }
+      atomic_hook_k<K>(b.labels, u, v, live, b.total_v, c);
+    }
+    if (seg == 0) {  // windows without locality: every arc on pi (one CTA per window)
+      for (unsigned long long j = blockIdx.x; j < n_plain; j += gridDim.x) {
+        const UnitInfo ui = unit_info(b, b.plain_units[j], W);
+        if (threadIdx.x == 0) s_bad = 0;
+        __syncthreads();
+        const int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
+        if (a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz) {
+          const int t0 = a0 + split_point<int>(a1 - a0, nwarps, warp);
+          const int t1 = a0 + split_point<int>(a1 - a0, nwarps, warp + 1);
+          if (t0 < t1)
+            hook_csr_range<int, SYM, false, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, nullptr, 0, 0,
+                                                    nullptr, nullptr, ui.vbase, &s_bad);
+        } else if (threadIdx.x == 0) {
+          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          s_bad = 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_bad && b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+      }
+    }
+    if (!grid_sync(c, epoch)) return;
+    // Multi-Jump over the vertices of multi-window graphs (global IDs), one CTA per window.
+    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+      const UnitInfo ui = unit_info(b, u, W);
+      if (ui.single) continue;
+      const int base = ui.vbase + ui.w0;
+      for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) {
+        const int x = base + i;
+        const int p = ld_pi(b.labels + x);
+        if (p != x) jump_from(b.labels, x, p, ld_pi(b.labels + p), b.total_v, c);
+      }
+    }
+    if (!grid_sync(c, epoch)) return;
+  }
+  // Global IDs of multi-window graphs -> graph-local labels.
+  for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const UnitInfo ui = unit_info(b, u, W);
+    if (ui.single) continue;
+    const int base = ui.vbase + ui.w0;
+    for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[base + i] -= ui.vbase;
+  }
+}
+
+template <bool SYM>
+__global__ void __launch_bounds__(kMaxBlockB, 1) k_batched(Batch b, Ctl c) {
+  extern __shared__ int dyn_smem[];
+  if (c.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) c.phase_ns[0] = now_ns();
+  batched_body<SYM>(b, dyn_smem, c);
+  if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + (c.phase_cap - 1), now_ns());
+}
+
+template <typename F>
+auto with_batched(bool sym, F&& f) {
+  return sym ? f(k_batched<true>) : f(k_batched<false>);
+}
+
+}  // namespace
+
+int batched_blocks_per_sm(bool sym, int block, int W) {
+  const size_t smem = tiled_smem_bytes(W, block);
+  return with_batched(sym, [&](auto k) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  });
+}
+
+cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
+  Batch b;
+  b.n_graphs = p.n_graphs;
+  b.v_off = p.v_off;
+  b.a_off = p.a_off;
+  b.rp_cat = p.rp_cat;
+  b.col_cat = p.col_cat;
+  b.labels = p.labels;
+  b.graph_status = p.graph_status;
+  b.unit_start = p.unit_start;
+  b.plain_units = p.plain_units;
+  b.plain_cap = p.plain_cap;
+  b.total_v = (int)p.total_v;
+  const size_t smem = tiled_smem_bytes(c.tile_w, s.block);
+  return with_batched(p.sym, [&](auto k) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)s.grid);
+    cfg.blockDim = dim3((unsigned)s.block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, b, c);
+  });
+}
+
+}  // namespace cc

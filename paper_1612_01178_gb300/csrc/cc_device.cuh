@@ -60,9 +60,13 @@ struct Ctl {
   int* ovf_units = nullptr;               // windows whose worklist appends overflowed
   int ovf_cap = 0;
   int segments_b = 0;                     // segments of the global phase (0 = 2|E'|/|V|)
+  int window_mode = 0;                    // batched: kWindowsSampled or kWindowsPlain
   unsigned long long* phase_ns = nullptr; // optional per-barrier timestamps (block 0)
   int phase_cap = 0;
 };
+
+// How the batched kernel hooks windows of multi-window graphs.
+enum WindowMode : int { kWindowsSampled = 0, kWindowsPlain = 1 };
 
 // DevStatus::counters[0..1] are the work counters of the dynamically scheduled phases.
 constexpr int kWorkCounters = 2;
@@ -479,7 +483,8 @@ template <typename OffT, bool SYM, bool TILED, int K>
 __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                                int V, OffT t0, OffT t1, const Ctl& c, int lo_row,
                                                int* lp = nullptr, int wbase = 0, int W = 0,
-                                               WarpSink* sink = nullptr, volatile int* ovf = nullptr) {
+                                               WarpSink* sink = nullptr, volatile int* ovf = nullptr,
+                                               int vbase = 0, volatile int* bad = nullptr) {
   const int lane = threadIdx.x & 31;
   int r = warp_row_search<OffT>(rp, lo_row, V, t0);
   int vn[K];
@@ -514,7 +519,10 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         u[j] = resolve_row<OffT>(rp, V, r, valid ? a : bj, valid, rem < 31 ? (int)rem : 31);
         if (valid) {
           const bool in_range = (unsigned)v[j] < (unsigned)V && (unsigned)u[j] < (unsigned)V;
-          if (!in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a);
+          if (!in_range) {
+            raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a);
+            if (bad) *bad = 1;
+          }
           live[j] = in_range && !(SYM ? (u[j] >= v[j]) : (u[j] == v[j]));
         }
       }
@@ -528,7 +536,14 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         sink_push(*sink, live[j] && !local, u[j], v[j], c, ovf);
       }
     } else {
-      atomic_hook_k<K>(pi, u, v, live, V, c);
+      if (vbase != 0) {  // graph of a batch: hook global IDs
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          u[j] += vbase;
+          v[j] += vbase;
+        }
+      }
+      atomic_hook_k<K>(pi, u, v, live, vbase + V, c);
     }
   }
   if (TILED) sink_flush(*sink, c, ovf);
@@ -612,16 +627,92 @@ __device__ __forceinline__ void load_group(const int* __restrict__ col, OffT x0,
   }
 }
 
-// Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window.
+// Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window. IDs
+// are local to the graph (< V); worklist entries get vbase added (the graph's first vertex in a
+// batch). `bad` records an endpoint outside [0, V).
 template <bool SYM>
 __device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, long long a, int V, int w0, int nrows,
-                                            int* lp, WarpSink& sink, volatile int* ovf, const Ctl& c) {
+                                            int* lp, WarpSink& sink, volatile int* ovf, volatile int* bad, int vbase,
+                                            const Ctl& c) {
   const bool in_range = has && (unsigned)v < (unsigned)V;
-  if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+  if (has && !in_range) {
+    raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+    *bad = 1;
+  }
   const bool live = in_range && (SYM ? (v > u) : (v != u));
   const bool local = live && (unsigned)(v - w0) < (unsigned)nrows;
   if (local) local_hook(lp, i, v - w0);
-  sink_push(sink, live && !local, u, v, c, ovf);
+  sink_push(sink, live && !local, u + vbase, v + vbase, c, ovf);
+}
+
+// Phase A of one window [w0, w0 + nrows) of a graph with V vertices and nnz arcs (rows rp,
+// arcs col, graph-local IDs), by the whole CTA: lp must hold lp[i] = i on entry (and a barrier
+// must separate that from this call); on return (after a barrier) lp holds the window's local
+// forest. Warps take 32-row chunks (one row per lane) in an interleaved order, so the CTA sweeps
+// the window roughly in ID order and new vertices mostly join components that already have
+// short paths to their roots. Loads run ahead of the hooks: row offsets two chunks ahead, the
+// first kGroup arcs of each row one chunk ahead. Rows of more than kHeavyRow arcs are walked by
+// the whole warp, 32 arcs at a time.
+template <typename OffT, bool SYM>
+__device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, const int* __restrict__ col, int V,
+                                               OffT nnz, int w0, int nrows, int vbase, int* lp, WarpSink& sink,
+                                               volatile int* ovf, volatile int* bad, const Ctl& c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int step = nwarps * 32;
+  const int r_begin = warp * 32;
+  const int r_end = nrows;
+  if (r_begin < r_end) {  // warp-uniform
+    OffT a0, a1, na0, na1;
+    int v[kGroup], nv[kGroup];
+    load_row_span<OffT>(rp, w0, r_begin + lane, r_end, a0, a1);
+    check_span<OffT>(a0, a1, nnz, w0 + r_begin + lane, c);
+    load_group<OffT>(col, a0, a1, 0, v);
+    load_row_span<OffT>(rp, w0, r_begin + step + lane, r_end, na0, na1);
+    for (int base = r_begin; base < r_end; base += step) {
+      check_span<OffT>(na0, na1, nnz, w0 + base + step + lane, c);
+      load_group<OffT>(col, na0, na1, 0, nv);
+      OffT nna0, nna1;
+      load_row_span<OffT>(rp, w0, base + 2 * step + lane, r_end, nna0, nna1);
+      const int i = base + lane;
+      const int u = w0 + i;
+      const long long deg = (long long)(a1 - a0);
+      const bool heavy = deg > kHeavyRow;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j)
+        phase_a_arc<SYM>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, ovf, bad, vbase,
+                         c);
+      const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
+      for (int g = 1; g * kGroup < maxdeg; ++g) {
+        int w[kGroup];
+        load_group<OffT>(col, a0, heavy ? a0 : a1, g, w);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+          phase_a_arc<SYM>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0, nrows,
+                           lp, sink, ovf, bad, vbase, c);
+      }
+      unsigned hv = __ballot_sync(kFull, heavy);
+      while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
+        const int h = __ffs(hv) - 1;
+        hv &= hv - 1;
+        const int hi = __shfl_sync(kFull, i, h);
+        const OffT h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
+        for (OffT bb = h0; bb < h1; bb += 32) {
+          const OffT a = bb + lane;
+          const bool has = a < h1;
+          const int vv = has ? ld_stream(col + a) : 0;
+          phase_a_arc<SYM>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, ovf, bad, vbase, c);
+        }
+      }
+      a0 = na0;
+      a1 = na1;
+      na0 = nna0;
+      na1 = nna1;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) v[j] = nv[j];
+    }
+  }
+  sink_flush(sink, c, ovf);
+  __syncthreads();
 }
 
 // Two-phase hierarchical Atomic-Hook, phase A. The vertices are cut into windows of W
@@ -638,18 +729,18 @@ template <typename OffT, bool SYM>
 __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                               int V, OffT nnz, int* smem, const Ctl& c) {
   __shared__ unsigned long long s_unit;
-  __shared__ int s_ovf;
+  __shared__ int s_ovf, s_bad;
   const int W = c.tile_w;
   int* lp = smem;
   const long long n_units = ((long long)V + W - 1) / W;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   WarpSink sink;
-  sink.buf = reinterpret_cast<int2*>(smem + W) + warp * kSinkPairs;
+  sink.buf = reinterpret_cast<int2*>(smem + W) + (threadIdx.x >> 5) * kSinkPairs;
   sink.count = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = atomicAdd(&c.st->counters[0], 1ull);
       s_ovf = 0;
+      s_bad = 0;
     }
     __syncthreads();
     const unsigned long long k = s_unit;
@@ -658,64 +749,7 @@ __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const
     const int nrows = (V - w0) < W ? (V - w0) : W;
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = i;
     __syncthreads();
-    // Warps take 32-row chunks (one row per lane) in an interleaved order, so the CTA sweeps
-    // the window roughly in ID order and new vertices mostly join components that already have
-    // short paths to their roots. Loads run ahead of the hooks: row offsets two chunks ahead,
-    // the first kGroup arcs of each row one chunk ahead.
-    const int step = nwarps * 32;
-    const int r_begin = warp * 32;
-    const int r_end = nrows;
-    if (r_begin < r_end) {  // warp-uniform
-      OffT a0, a1, na0, na1;
-      int v[kGroup], nv[kGroup];
-      load_row_span<OffT>(rp, w0, r_begin + lane, r_end, a0, a1);
-      check_span<OffT>(a0, a1, nnz, w0 + r_begin + lane, c);
-      load_group<OffT>(col, a0, a1, 0, v);
-      load_row_span<OffT>(rp, w0, r_begin + step + lane, r_end, na0, na1);
-      for (int base = r_begin; base < r_end; base += step) {
-        check_span<OffT>(na0, na1, nnz, w0 + base + step + lane, c);
-        load_group<OffT>(col, na0, na1, 0, nv);
-        OffT nna0, nna1;
-        load_row_span<OffT>(rp, w0, base + 2 * step + lane, r_end, nna0, nna1);
-        const int i = base + lane;
-        const int u = w0 + i;
-        const long long deg = (long long)(a1 - a0);
-        const bool heavy = deg > kHeavyRow;
-#pragma unroll
-        for (int j = 0; j < kGroup; ++j)
-          phase_a_arc<SYM>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, &s_ovf, c);
-        const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
-        for (int g = 1; g * kGroup < maxdeg; ++g) {
-          int w[kGroup];
-          load_group<OffT>(col, a0, heavy ? a0 : a1, g, w);
-#pragma unroll
-          for (int j = 0; j < kGroup; ++j)
-            phase_a_arc<SYM>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0,
-                             nrows, lp, sink, &s_ovf, c);
-        }
-        unsigned hv = __ballot_sync(kFull, heavy);
-        while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
-          const int h = __ffs(hv) - 1;
-          hv &= hv - 1;
-          const int hi = __shfl_sync(kFull, i, h);
-          const OffT h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
-          for (OffT bb = h0; bb < h1; bb += 32) {
-            const OffT a = bb + lane;
-            const bool has = a < h1;
-            const int vv = has ? ld_stream(col + a) : 0;
-            phase_a_arc<SYM>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, &s_ovf, c);
-          }
-        }
-        a0 = na0;
-        a1 = na1;
-        na0 = nna0;
-        na1 = nna1;
-#pragma unroll
-        for (int j = 0; j < kGroup; ++j) v[j] = nv[j];
-      }
-    }
-    sink_flush(sink, c, &s_ovf);
-    __syncthreads();
+    phase_a_window<OffT, SYM>(rp, col, V, nnz, w0, nrows, 0, lp, sink, &s_ovf, &s_bad, c);
     volatile int* vlp = lp;
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) pi[w0 + i] = w0 + lfind(vlp, i);
     if (threadIdx.x == 0 && s_ovf) {

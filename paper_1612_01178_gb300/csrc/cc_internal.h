@@ -47,6 +47,24 @@ cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cud
 // Returns the number of launches issued in *launches.
 cudaError_t launch_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream, int* launches);
 
+// A batch of graphs over a graph-offset table (see cc_batched.cu).
+struct BatchProblem {
+  int n_graphs;
+  const long long* v_off;
+  const long long* a_off;
+  const int* rp_cat;
+  const int* col_cat;
+  int* labels;
+  int* graph_status;
+  long long* unit_start;
+  int* plain_units;
+  int plain_cap;
+  long long total_v;
+  bool sym;
+};
+int batched_blocks_per_sm(bool sym, int block, int W);
+cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+
 // Locality sample: out[0] += sampled arcs with both ends in one window of W vertices,
 // out[1] += sampled arcs (out must be zeroed by the caller).
 cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* out, int threads, cudaStream_t stream);

@@ -14,6 +14,9 @@ Workloads (seeded synthetic graphs, generated on the host before timing):
   batched : 4096 independent graphs, |V| log-uniform in [1e3, 1e6], family uniform over
             {ER avg degree 4..32, 2D grid p = 0.9, R-MAT edge factor 8}; one batched launch per step
             (metric: graphs/s), with the single-graph kernel run graph by graph timed beside it
+  serve   : Poisson arrivals of CC requests at 100..5000 req/s, each an ER (degree 4..32) or R-MAT
+            (edge factor 8) graph with E log-uniform in [1e4, 2e7] (a pool of pre-generated graphs in
+            pinned host memory); continuous batching vs one request at a time (metric: p50/p99 latency)
 """
 from __future__ import annotations
 
@@ -423,6 +426,88 @@ def run_batched(args, rank, world, local_rank):
     return 0 if parity.startswith("bit-exact") and bg_ok else 3
 
 
+def serve_pool(n: int, seed: int = 1):
+    """Pool of request graphs: ER or R-MAT with equal odds, E log-uniform in [1e4, 2e7]."""
+    rng = np.random.default_rng(seed)
+    graphs = []
+    for i in range(n):
+        E = gen.loguniform_int(rng, 1e4, 2e7)
+        if rng.random() < 0.5:
+            d = int(rng.integers(4, 33))
+            graphs.append(gen.er_csr(max(2, -(-2 * E // d)), E, seed=5000 + i))
+        else:
+            scale = max(4, int(round(np.log2(max(16, E / 8)))))
+            graphs.append(gen.rmat_csr(scale, 8, seed=5000 + i))
+    return graphs
+
+
+def run_serve(args, rank, world, local_rank):
+    import torch
+    from paper_1612_01178_gb300.serve import Request, SequentialServer, Server, latency_summary
+
+    if rank != 0:  # replicas only; the serving measurement is per GPU
+        return 0
+    torch.cuda.set_device(local_rank)
+    t0 = time.perf_counter()
+    graphs = serve_pool(args.pool, seed=1)
+    pinned = [(torch.from_numpy(g.row_ptr).pin_memory().numpy(), torch.from_numpy(g.col).pin_memory().numpy())
+              for g in graphs]
+    gen_s = time.perf_counter() - t0
+    budget = Server.budget_from_free_memory(0.4, local_rank, avg_degree=20.0)
+    srv = Server(local_rank, max_batch=args.max_batch, **budget)
+    seq = SequentialServer(local_rank)
+    rng = np.random.default_rng(7)
+    rates = [float(r) for r in args.rates.split(",")]
+
+    def stream(rate, n):
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+        pick = rng.integers(0, len(graphs), n)
+        return [Request(i, float(arrivals[i]), *pinned[pick[i]]) for i in range(n)], pick
+
+    # warm-up: every pool graph once through both servers; the labels are checked against the
+    # oracle and then serve as the expected answer of every later request for that graph
+    import oracle
+    warm = [Request(i, 0.0, *pinned[i]) for i in range(len(graphs))]
+    srv.run(warm)
+    seq.run([Request(r.rid, 0.0, r.row_ptr, r.col) for r in warm])
+    expect = [r.labels.copy() for r in warm]
+    parity = "bit-exact"
+    for i, g in enumerate(graphs):
+        if not np.array_equal(expect[i], oracle.labels_uf_csr(g.row_ptr, g.col)[0]):
+            parity = "MISMATCH (graph %d)" % i
+    results = []
+    sampler = ClockSampler(device_uuid(torch, torch.device("cuda", local_rank), local_rank))
+    sampler.start()
+    for rate in rates:
+        n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
+        reqs, pick = stream(rate, n)
+        out = srv.run(reqs)
+        s = latency_summary(out)
+        same = all(np.array_equal(r.labels, expect[i]) for r, i in zip(out, pick))
+        base = [Request(r.rid, r.arrival, r.row_ptr, r.col) for r in reqs]
+        b = latency_summary(seq.run(base))
+        if not same:
+            parity = "MISMATCH (continuous batching at %g req/s)" % rate
+        results.append({"rate_req_s": rate, "requests": n, "continuous_batching": s, "one_at_a_time": b,
+                        "batches": len(srv.batches), "mean_batch": n / max(1, len(srv.batches))})
+        srv.batches.clear()
+    clocks = sampler.stop()
+    srv.close()
+    seq.close()
+    ref = next((x for x in results if x["rate_req_s"] == 1000.0), results[len(results) // 2])
+    line = {
+        "metric": "served p50/p99 latency", "value": ref["continuous_batching"]["p99_ms"], "unit": "ms (p99)",
+        "n_gpus": 1, "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serve", "pool_graphs": len(graphs), "rates": rates, "arena_elems": budget,
+                   "max_batch": args.max_batch, "flags": "CC_FLAG_SYMMETRIC", "generation_s": round(gen_s, 1),
+                   "value_is": "p99 latency at %g req/s" % ref["rate_req_s"]},
+        "rates": results, "clocks": clocks, "parity": parity,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if parity == "bit-exact" else 3
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1612_01178_gb300 as ccl
@@ -601,8 +686,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="grid")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve"], default="grid")
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serve: arrival rates (req/s)")
+    ap.add_argument("--pool", type=int, default=128, help="serve: distinct request graphs")
+    ap.add_argument("--seconds", type=float, default=1.5, help="serve: arrival span per rate")
+    ap.add_argument("--min-requests", type=int, default=150)
+    ap.add_argument("--max-requests", type=int, default=3000)
+    ap.add_argument("--max-batch", type=int, default=1024)
     ap.add_argument("--mode", choices=["persistent", "multi"], default="persistent")
     ap.add_argument("--segments", type=int, default=0, help="0 = the average degree (Section III-B)")
     ap.add_argument("--tile", type=int, default=0, help="hook window: 0 = automatic, -1 = plain hook")
@@ -617,7 +708,7 @@ def main(argv=None):
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    run = run_batched if args.workload == "batched" else run_ours
+    run = {"batched": run_batched, "serve": run_serve}.get(args.workload, run_ours)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -165,6 +165,28 @@ cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertice
                             const int64_t* v_off, const int64_t* a_off, const int32_t* row_ptr_cat,
                             const int32_t* col_idx_cat, int32_t* labels_cat, int32_t* graph_status);
 
+/* One graph of a descriptor-mode batch: element offsets of its labels (label_off, V
+   entries), row offsets (row_off, V + 1 graph-local offsets) and arcs (arc_off, n_arcs
+   graph-local IDs) inside three device arenas. */
+typedef struct cc_graph_desc {
+  int64_t label_off;
+  int64_t row_off;
+  int64_t arc_off;
+  int64_t n_arcs;
+  int32_t n_vertices;
+  int32_t reserved; /* 0 */
+} cc_graph_desc;
+
+/* cc_labels_batched for graphs placed anywhere in three device arenas (a serving loop keeps
+ * requests wherever its allocator put them). descs is a device array [n_graphs]; label ranges
+ * [label_off, label_off + n_vertices) must not overlap. A descriptor that does not fit its arena
+ * sizes is reported in graph_status (and the status word) and its graph is skipped.
+ * label_arena_elems must be below 2^31. Results are graph-local minimum IDs at label_off. */
+cc_status cc_labels_batched_desc(cc_ctx* ctx, int32_t n_graphs, const cc_graph_desc* descs,
+                                 const int32_t* row_arena, int64_t row_arena_elems, const int32_t* arc_arena,
+                                 int64_t arc_arena_elems, int32_t* label_arena, int64_t label_arena_elems,
+                                 int32_t* graph_status);
+
 /* cc_labels_csr with HOST buffers: copies row_ptr and col_idx from host memory
    (pinned memory gives full copy bandwidth) into context-owned device buffers,
    runs the method, copies the labels back into the host array `labels`, and

@@ -91,6 +91,7 @@ SIGNATURES = {
     "cc_labels_coo": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "cc_labels_csr_host": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
     "cc_labels_batched": (ctypes.c_int, [_vp, _i32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "cc_labels_batched_desc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "cc_sync": (ctypes.c_int, [_vp]),
     "cc_last_run_info": (ctypes.c_int, [_vp, ctypes.POINTER(cc_run_info)]),
     "cc_last_error_message": (ctypes.c_char_p, [_vp]),

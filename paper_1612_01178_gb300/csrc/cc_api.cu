@@ -438,23 +438,11 @@ cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const 
   return st;
 }
 
-cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertices, int64_t total_arcs,
-                            const int64_t* v_off, const int64_t* a_off, const int32_t* row_ptr_cat,
-                            const int32_t* col_idx_cat, int32_t* labels_cat, int32_t* graph_status) {
-  if (!ctx) return CC_ERR_INVALID_ARG;
-  if (n_graphs < 0 || total_vertices < 0 || total_vertices >= INT32_MAX || total_arcs < 0) return CC_ERR_INVALID_ARG;
-  if (n_graphs > 0 && (!v_off || !a_off || !row_ptr_cat)) return CC_ERR_INVALID_ARG;
-  if (total_vertices > 0 && !labels_cat) return CC_ERR_INVALID_ARG;
-  if (total_arcs > 0 && (!col_idx_cat || total_vertices == 0)) return CC_ERR_INVALID_ARG;
-  if (overlaps(labels_cat, (size_t)total_vertices * 4, col_idx_cat, (size_t)total_arcs * 4) ||
-      overlaps(labels_cat, (size_t)total_vertices * 4, row_ptr_cat, (size_t)(total_vertices + n_graphs) * 4))
-    return CC_ERR_INVALID_ARG;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return CC_ERR_CUDA;
-  ctx->last = cc_run_info{};
+// Launches one batch (offset-table or descriptor mode) on the context's stream.
+static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arcs) {
   const cc_options& o = ctx->opt;
-  if (n_graphs == 0) return (o.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
-
+  const int n_graphs = p.n_graphs;
+  const long long total_vertices = p.total_v;
   const int W = o.tile_vertices > 0 ? window_for(INT32_MAX, o.tile_vertices) : kDefaultTileVertices;
   int block = o.block > 0 ? o.block : kTiledBlock;
   const bool sym = (o.flags & CC_FLAG_SYMMETRIC) != 0;
@@ -488,23 +476,14 @@ cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertice
   c.window_mode = o.tile_vertices == -1 ? cc::kWindowsPlain : cc::kWindowsSampled;
   c.skip_arrival_block = ctx->skip_arrival_block;
   ctx->skip_arrival_block = -1;
-
-  cc::BatchProblem p{};
-  p.n_graphs = n_graphs;
-  p.v_off = reinterpret_cast<const long long*>(v_off);
-  p.a_off = reinterpret_cast<const long long*>(a_off);
-  p.rp_cat = row_ptr_cat;
-  p.col_cat = col_idx_cat;
-  p.labels = labels_cat;
-  p.graph_status = graph_status;
   p.unit_start = ctx->d_unit_start;
   p.plain_units = ctx->d_ovf;
   p.plain_cap = (int)std::min<size_t>(ctx->d_ovf_n, INT32_MAX);
-  p.total_v = total_vertices;
   p.sym = sym;
 
   cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
-  if (e == cudaSuccess && graph_status) e = cudaMemsetAsync(graph_status, 0, sizeof(int32_t) * n_graphs, ctx->stream);
+  if (e == cudaSuccess && p.graph_status)
+    e = cudaMemsetAsync(p.graph_status, 0, sizeof(int32_t) * n_graphs, ctx->stream);
   if (e == cudaSuccess && (o.flags & CC_FLAG_PHASE_TIMES)) {
     if (!ctx->d_phase && cudaMalloc(&ctx->d_phase, kPhaseSlots * sizeof(unsigned long long)) != cudaSuccess) {
       ctx->d_phase = nullptr;
@@ -531,6 +510,63 @@ cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertice
   ctx->last = info;
   if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
   return CC_OK;
+}
+
+cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertices, int64_t total_arcs,
+                            const int64_t* v_off, const int64_t* a_off, const int32_t* row_ptr_cat,
+                            const int32_t* col_idx_cat, int32_t* labels_cat, int32_t* graph_status) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_graphs < 0 || total_vertices < 0 || total_vertices >= INT32_MAX || total_arcs < 0) return CC_ERR_INVALID_ARG;
+  if (n_graphs > 0 && (!v_off || !a_off || !row_ptr_cat)) return CC_ERR_INVALID_ARG;
+  if (total_vertices > 0 && !labels_cat) return CC_ERR_INVALID_ARG;
+  if (total_arcs > 0 && (!col_idx_cat || total_vertices == 0)) return CC_ERR_INVALID_ARG;
+  if (overlaps(labels_cat, (size_t)total_vertices * 4, col_idx_cat, (size_t)total_arcs * 4) ||
+      overlaps(labels_cat, (size_t)total_vertices * 4, row_ptr_cat, (size_t)(total_vertices + n_graphs) * 4))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  if (n_graphs == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  cc::BatchProblem p{};
+  p.n_graphs = n_graphs;
+  p.v_off = reinterpret_cast<const long long*>(v_off);
+  p.a_off = reinterpret_cast<const long long*>(a_off);
+  p.rp_cat = row_ptr_cat;
+  p.col_cat = col_idx_cat;
+  p.labels = labels_cat;
+  p.graph_status = graph_status;
+  p.total_v = total_vertices;
+  return run_batch(ctx, p, total_arcs);
+}
+
+cc_status cc_labels_batched_desc(cc_ctx* ctx, int32_t n_graphs, const cc_graph_desc* descs,
+                                 const int32_t* row_arena, int64_t row_arena_elems, const int32_t* arc_arena,
+                                 int64_t arc_arena_elems, int32_t* label_arena, int64_t label_arena_elems,
+                                 int32_t* graph_status) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_graphs < 0 || label_arena_elems < 0 || label_arena_elems >= INT32_MAX || row_arena_elems < 0 ||
+      arc_arena_elems < 0)
+    return CC_ERR_INVALID_ARG;
+  if (n_graphs > 0 && (!descs || !row_arena || !label_arena)) return CC_ERR_INVALID_ARG;
+  if (overlaps(label_arena, (size_t)label_arena_elems * 4, arc_arena, (size_t)arc_arena_elems * 4) ||
+      overlaps(label_arena, (size_t)label_arena_elems * 4, row_arena, (size_t)row_arena_elems * 4))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  if (n_graphs == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  static_assert(sizeof(cc_graph_desc) == sizeof(cc::GraphDesc), "descriptor layouts must agree");
+  cc::BatchProblem p{};
+  p.n_graphs = n_graphs;
+  p.desc = reinterpret_cast<const cc::GraphDesc*>(descs);
+  p.rp_cat = row_arena;
+  p.col_cat = arc_arena;
+  p.labels = label_arena;
+  p.graph_status = graph_status;
+  p.total_v = label_arena_elems;
+  p.row_elems = row_arena_elems;
+  p.arc_elems = arc_arena_elems;
+  return run_batch(ctx, p, std::max<long long>(arc_arena_elems, 1));
 }
 
 static cc_status grow(cc_ctx* ctx, void** buf, size_t* have, size_t need) {

@@ -29,6 +29,7 @@ constexpr int kMaxBlockB = 1024;
 
 struct Batch {
   int n_graphs;
+  const GraphDesc* desc;   // descriptor mode (nullptr: offset tables v_off / a_off)
   const long long* v_off;
   const long long* a_off;
   const int* rp_cat;
@@ -38,10 +39,28 @@ struct Batch {
   long long* unit_start;   // [n_graphs + 1] first window of each graph (filled by the kernel)
   int* plain_units;        // windows hooked arc by arc in phase B
   int plain_cap;
-  int total_v;
+  int total_v;             // label arena size (batch-global IDs are below it)
+  long long row_elems;     // descriptor mode: row-offset arena size
+  long long arc_elems;     // descriptor mode: arc arena size
 };
 
 __device__ __forceinline__ long long units_of(long long vg, int W) { return vg <= 0 ? 0 : (vg + W - 1) / W; }
+
+// Vertices of graph g; a descriptor that does not fit its arenas is reported (per graph and
+// in the status word) and its graph gets no windows, so nothing reads or writes through it.
+__device__ __forceinline__ long long graph_vertices(const Batch& b, int g, const Ctl& c) {
+  if (!b.desc) return b.v_off[g + 1] - b.v_off[g];
+  const GraphDesc d = b.desc[g];
+  const bool ok = d.n_vertices >= 0 && d.n_arcs >= 0 && d.n_arcs <= 0x7fffffffLL && d.label_off >= 0 &&
+                  d.label_off + d.n_vertices <= (long long)b.total_v && d.row_off >= 0 &&
+                  d.row_off + d.n_vertices + 1 <= b.row_elems && d.arc_off >= 0 && d.arc_off + d.n_arcs <= b.arc_elems;
+  if (!ok) {
+    raise_error(c.st, kErrOutOfRange, kSiteValidate, (long long)g);
+    if (b.graph_status) b.graph_status[g] = kErrOutOfRange;
+    return 0;
+  }
+  return d.n_vertices;
+}
 
 // Block-wide inclusive scan of one value per thread (blockDim.x a multiple of 32).
 __device__ __forceinline__ long long block_scan(long long x, long long* warp_sums, long long* total) {
@@ -91,16 +110,27 @@ struct UnitInfo {
 __device__ __forceinline__ UnitInfo unit_info(const Batch& b, long long u, int W) {
   UnitInfo ui;
   ui.g = graph_of_unit(b.unit_start, b.n_graphs, u);
-  const long long vo = b.v_off[ui.g];
-  ui.vg = (int)(b.v_off[ui.g + 1] - vo);
+  long long vo, ro, ao;
+  if (b.desc) {
+    const GraphDesc d = b.desc[ui.g];
+    vo = d.label_off;
+    ro = d.row_off;
+    ao = d.arc_off;
+    ui.vg = d.n_vertices;
+    ui.nnz = d.n_arcs;
+  } else {
+    vo = b.v_off[ui.g];
+    ro = vo + ui.g;
+    ao = b.a_off[ui.g];
+    ui.vg = (int)(b.v_off[ui.g + 1] - vo);
+    ui.nnz = b.a_off[ui.g + 1] - ao;
+  }
   ui.vbase = (int)vo;
   const long long k = u - b.unit_start[ui.g];
   ui.single = (b.unit_start[ui.g + 1] - b.unit_start[ui.g]) == 1;
   ui.w0 = (int)(k * W);
   ui.nrows = (ui.vg - ui.w0) < W ? (ui.vg - ui.w0) : W;
-  const long long ao = b.a_off[ui.g];
-  ui.nnz = b.a_off[ui.g + 1] - ao;
-  ui.rp = b.rp_cat + vo + ui.g;
+  ui.rp = b.rp_cat + ro;
   ui.col = b.col_cat + ao;
   return ui;
 }
@@ -142,7 +172,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     if (threadIdx.x == 0) b.unit_start[0] = 0;
     for (int base = 0; base < b.n_graphs; base += blockDim.x) {
       const int g = base + threadIdx.x;
-      const long long n = g < b.n_graphs ? units_of(b.v_off[g + 1] - b.v_off[g], W) : 0;
+      const long long n = g < b.n_graphs ? units_of(graph_vertices(b, g, c), W) : 0;
       const long long incl = block_scan(n, s_warp_sums, &s_total);
       if (g < b.n_graphs) b.unit_start[g + 1] = carry + incl;
       carry += s_total;
@@ -318,6 +348,7 @@ int batched_blocks_per_sm(bool sym, int block, int W) {
 cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
   Batch b;
   b.n_graphs = p.n_graphs;
+  b.desc = p.desc;
   b.v_off = p.v_off;
   b.a_off = p.a_off;
   b.rp_cat = p.rp_cat;
@@ -328,6 +359,8 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
   b.plain_units = p.plain_units;
   b.plain_cap = p.plain_cap;
   b.total_v = (int)p.total_v;
+  b.row_elems = p.row_elems;
+  b.arc_elems = p.arc_elems;
   const size_t smem = tiled_smem_bytes(c.tile_w, s.block);
   return with_batched(p.sym, [&](auto k) {
     if (smem > 48 * 1024) {

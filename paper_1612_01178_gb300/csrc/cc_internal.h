@@ -47,9 +47,21 @@ cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cud
 // Returns the number of launches issued in *launches.
 cudaError_t launch_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream, int* launches);
 
-// A batch of graphs over a graph-offset table (see cc_batched.cu).
+// One graph of a descriptor-mode batch: its labels, row offsets and arcs sit at these element
+// offsets of the label, row-offset and arc arenas (layout-compatible with cc_graph_desc).
+struct GraphDesc {
+  long long label_off;
+  long long row_off;
+  long long arc_off;
+  long long n_arcs;
+  int n_vertices;
+  int reserved;
+};
+
+// A batch of graphs over a graph-offset table or descriptors (see cc_batched.cu).
 struct BatchProblem {
   int n_graphs;
+  const GraphDesc* desc;
   const long long* v_off;
   const long long* a_off;
   const int* rp_cat;
@@ -59,7 +71,9 @@ struct BatchProblem {
   long long* unit_start;
   int* plain_units;
   int plain_cap;
-  long long total_v;
+  long long total_v;    // label arena size
+  long long row_elems;  // descriptor mode: arena sizes
+  long long arc_elems;
   bool sym;
 };
 int batched_blocks_per_sm(bool sym, int block, int W);

@@ -196,11 +196,42 @@ def run_reference_batched(args):
     return 0
 
 
+def run_reference_serve(args):
+    """The oracle serving the request pool one request at a time: per-request service time."""
+    import oracle
+    graphs = serve_pool(min(args.pool, 32), seed=1)
+    for g in graphs[:args.warmup]:
+        oracle.labels_uf_csr(g.row_ptr, g.col)
+    lat = []
+    for k in range(max(1, args.steps)):
+        for g in graphs:
+            t1 = time.perf_counter()
+            oracle.labels_uf_csr(g.row_ptr, g.col)
+            lat.append(time.perf_counter() - t1)
+    lat_ms = np.array(lat) * 1000
+    line = {
+        "impl": "reference", "metric": "served p50/p99 latency", "value": float(np.percentile(lat_ms, 99)),
+        "unit": "ms (p99)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(lat_ms.mean()), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serve", "pool_graphs": len(graphs), "value_is": "p99 service time, no queueing"},
+        "p50_ms": float(np.percentile(lat_ms, 50)),
+        "cpu_baseline": {"value": float(np.percentile(lat_ms, 99)), "unit": "ms (p99)", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(graphs)} request graphs x {max(1, args.steps)}, union-find oracle"},
+        "e2e": {"value": float(np.percentile(lat_ms, 99)), "unit": "ms (p99)", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     if args.workload == "batched":
         return run_reference_batched(args)
+    if args.workload == "serve":
+        return run_reference_serve(args)
     name, make = WORKLOADS[args.workload]
     g = make()
     import oracle

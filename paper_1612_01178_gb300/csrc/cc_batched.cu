@@ -88,6 +88,13 @@ __device__ __forceinline__ long long block_scan(long long x, long long* warp_sum
   return r;
 }
 
+// How many CTAs share one window when there are too few windows to keep the grid busy.
+__device__ __forceinline__ unsigned long long split_factor(unsigned long long items, unsigned grid) {
+  if (items == 0) return 1;
+  unsigned long long f = (2ull * grid + items - 1) / items;
+  return f < 1 ? 1 : (f > 64 ? 64 : f);
+}
+
 // Graph owning window u: largest g with unit_start[g] <= u (graphs without vertices own none).
 __device__ __forceinline__ int graph_of_unit(const long long* unit_start, int n, long long u) {
   int lo = 0, hi = n;  // unit_start[lo] <= u < unit_start[hi]
@@ -270,13 +277,19 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       }
       atomic_hook_k<K>(b.labels, u, v, live, b.total_v, c);
     }
-    if (seg == 0) {  // windows without locality: every arc on pi (one CTA per window)
-      for (unsigned long long j = blockIdx.x; j < n_plain; j += gridDim.x) {
-        const UnitInfo ui = unit_info(b, b.plain_units[j], W);
+    if (seg == 0) {  // windows without locality: every arc on pi, each window split over `parts` CTAs
+      const unsigned long long parts = split_factor(n_plain, gridDim.x);
+      for (unsigned long long item = blockIdx.x; item < n_plain * parts; item += gridDim.x) {
+        const UnitInfo ui = unit_info(b, b.plain_units[item / parts], W);
+        const long long part = (long long)(item % parts);
         if (threadIdx.x == 0) s_bad = 0;
         __syncthreads();
-        const int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
+        int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
         if (a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz) {
+          const int p0 = a0 + split_point<int>(a1 - a0, (long long)parts, part);
+          const int p1 = a0 + split_point<int>(a1 - a0, (long long)parts, part + 1);
+          a0 = p0;
+          a1 = p1;
           const int t0 = a0 + split_point<int>(a1 - a0, nwarps, warp);
           const int t1 = a0 + split_point<int>(a1 - a0, nwarps, warp + 1);
           if (t0 < t1)
@@ -291,12 +304,16 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       }
     }
     if (!grid_sync(c, epoch)) return;
-    // Multi-Jump over the vertices of multi-window graphs (global IDs), one CTA per window.
-    for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
-      const UnitInfo ui = unit_info(b, u, W);
+    // Multi-Jump over the vertices of multi-window graphs (global IDs), windows split over CTAs.
+    const unsigned long long vparts = split_factor((unsigned long long)n_units, gridDim.x);
+    for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * vparts; item += gridDim.x) {
+      const UnitInfo ui = unit_info(b, (long long)(item / vparts), W);
       if (ui.single) continue;
+      const long long part = (long long)(item % vparts);
       const int base = ui.vbase + ui.w0;
-      for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) {
+      const int i0 = split_point<int>(ui.nrows, (long long)vparts, part);
+      const int i1 = split_point<int>(ui.nrows, (long long)vparts, part + 1);
+      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int x = base + i;
         const int p = ld_pi(b.labels + x);
         if (p != x) jump_from(b.labels, x, p, ld_pi(b.labels + p), b.total_v, c);
@@ -305,11 +322,15 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     if (!grid_sync(c, epoch)) return;
   }
   // Global IDs of multi-window graphs -> graph-local labels.
-  for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const UnitInfo ui = unit_info(b, u, W);
+  const unsigned long long cparts = split_factor((unsigned long long)n_units, gridDim.x);
+  for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * cparts; item += gridDim.x) {
+    const UnitInfo ui = unit_info(b, (long long)(item / cparts), W);
     if (ui.single) continue;
+    const long long part = (long long)(item % cparts);
     const int base = ui.vbase + ui.w0;
-    for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[base + i] -= ui.vbase;
+    const int i0 = split_point<int>(ui.nrows, (long long)cparts, part);
+    const int i1 = split_point<int>(ui.nrows, (long long)cparts, part + 1);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) b.labels[base + i] -= ui.vbase;
   }
 }
 

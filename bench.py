@@ -14,6 +14,9 @@ Workloads (seeded synthetic graphs, generated on the host before timing):
   batched : 4096 independent graphs, |V| log-uniform in [1e3, 1e6], family uniform over
             {ER avg degree 4..32, 2D grid p = 0.9, R-MAT edge factor 8}; one batched launch per step
             (metric: graphs/s), with the single-graph kernel run graph by graph timed beside it
+  ablation: the paper's Fig. 5 ladder on stand-ins for its Table I graphs (Soman et al.'s host loop,
+            + Multi-Jump, + Atomic-Hook with s = 1, + adaptive s, and this library's default path)
+  segsweep: the paper's Fig. 6: time vs segment count s on ER graphs across the degree spectrum
   serve   : Poisson arrivals of CC requests at 100..5000 req/s, each an ER (degree 4..32) or R-MAT
             (edge factor 8) graph with E log-uniform in [1e4, 2e7] (a pool of pre-generated graphs in
             pinned host memory); continuous batching vs one request at a time (metric: p50/p99 latency)
@@ -539,6 +542,116 @@ def run_serve(args, rank, world, local_rank):
     return 0 if parity == "bit-exact" else 3
 
 
+ABLATION_GRAPHS = {
+    # stand-ins for the paper's Table I (avg degree = arcs / vertices there as here)
+    "road (usa-osm-like): grid 4096^2 p=0.9": lambda: gen.workload_grid_4096(seed=1),
+    "social (soc-live-journal-like): R-MAT scale 22, ef 8": lambda: gen.rmat_csr(22, 8, seed=1),
+    "kron (kron-logn21-like): R-MAT scale 21, ef 43": lambda: gen.rmat_csr(21, 43, seed=1),
+}
+
+
+def time_labelling(ccl, torch, g, reps=5, **opts):
+    """Median device time (ms) of a labelling with the given options, plus its labels and run info."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    lab = torch.empty(g.n_vertices, dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    o = dict(flags=ccl.CC_FLAG_SYMMETRIC)
+    o.update(opts)
+    cc = ccl.ConnectedComponents(dev.index, **o)
+    ts = []
+    for k in range(reps + 1):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        cc.csr(rp, col, lab)
+        e1.record(torch.cuda.current_stream())
+        cc.sync()
+        wall = time.perf_counter() - t1
+        if k:  # the host-driven modes synchronise inside the call: take the wall time around it
+            ts.append(max(e0.elapsed_time(e1), 1000 * wall if o.get("mode", 0) >= 3 else 0.0))
+    info = cc.run_info()
+    out = lab.cpu().numpy()
+    cc.close()
+    return statistics.median(ts), out, info
+
+
+def run_ablation(args, rank, world, local_rank):
+    import torch
+    import oracle
+    import paper_1612_01178_gb300 as ccl
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    ladder = [
+        ("Soman et al. (Fig. 1 + Fig. 2 Hook/Jump, host loop)", dict(mode=ccl.cc.CC_MODE_SOMAN)),
+        ("+ Multi-Jump", dict(mode=ccl.cc.CC_MODE_SOMAN_MULTIJUMP)),
+        ("+ Atomic-Hook, s = 1 (Fig. 4 host loop)", dict(mode=ccl.CC_MODE_MULTI_LAUNCH, segments=1, tile_vertices=-1)),
+        ("+ adaptive s = 2|E|/|V| (Fig. 4 host loop)", dict(mode=ccl.CC_MODE_MULTI_LAUNCH, tile_vertices=-1)),
+        ("GB300 default (persistent, automatic hook)", dict()),
+    ]
+    rows = []
+    for gname, make in ABLATION_GRAPHS.items():
+        g = make()
+        want, _ = oracle.labels_uf_csr(g.row_ptr, g.col)
+        base = None
+        for vname, opts in ladder:
+            ms, out, info = time_labelling(ccl, torch, g, reps=args.steps, **opts)
+            base = base or ms
+            rows.append({"graph": gname, "V": g.n_vertices, "arcs": g.nnz, "avg_degree": g.nnz / g.n_vertices,
+                         "variant": vname, "ms": ms, "speedup_vs_soman": base / ms,
+                         "launches": info["launches"], "host_round_trips": info["host_round_trips"],
+                         "segments": info["segments"], "bit_exact": bool(np.array_equal(out, want))})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "Fig. 5 ablation: time per labelling", "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "data": "synthetic", "config": {"workload": "ablation"},
+            "rows": rows, "parity": "bit-exact" if all(r["bit_exact"] for r in rows) else "MISMATCH"}
+    print(json.dumps(line), flush=True)
+    return 0 if line["parity"] == "bit-exact" else 3
+
+
+def run_segsweep(args, rank, world, local_rank):
+    import torch
+    import oracle
+    import paper_1612_01178_gb300 as ccl
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local_rank)
+    V = 1 << 20
+    rows = []
+    for d in (2, 4, 8, 16, 32, 64, 128):
+        g = gen.er_csr(V, d * V // 2, seed=11)
+        want, _ = oracle.labels_uf_csr(g.row_ptr, g.col)
+        heuristic = max(1, round(g.nnz / V))
+        svals = sorted({1, 2, 4, 8, 16, 32, 64, 128, 256, 512, heuristic, 2 * heuristic, 4 * heuristic})
+        svals = [s for s in svals if s <= 4 * max(1, heuristic)]
+        for label, base_opts in (("Fig. 4 host loop (plain hook)", dict(mode=ccl.CC_MODE_MULTI_LAUNCH, tile_vertices=-1)),
+                                 ("persistent (plain hook)", dict(mode=ccl.CC_MODE_PERSISTENT, tile_vertices=-1))):
+            t1 = None
+            for s in svals:
+                ms, out, _ = time_labelling(ccl, torch, g, reps=args.steps, segments=s, **base_opts)
+                t1 = t1 or ms
+                rows.append({"avg_degree": d, "heuristic_s": heuristic, "driver": label, "s": s, "ms": ms,
+                             "speedup_vs_s1": t1 / ms, "bit_exact": bool(np.array_equal(out, want))})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    best = {}
+    for r in rows:
+        k = (r["avg_degree"], r["driver"])
+        if k not in best or r["ms"] < best[k]["ms"]:
+            best[k] = r
+    line = {"metric": "Fig. 6 segmentation sweep: time per labelling vs s", "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "data": "synthetic", "config": {"workload": "segsweep", "V": V},
+            "best": [{"avg_degree": k[0], "driver": k[1], "best_s": v["s"], "heuristic_s": v["heuristic_s"],
+                      "speedup_vs_s1": v["speedup_vs_s1"]} for k, v in sorted(best.items())],
+            "rows": rows, "parity": "bit-exact" if all(r["bit_exact"] for r in rows) else "MISMATCH"}
+    print(json.dumps(line), flush=True)
+    return 0 if line["parity"] == "bit-exact" else 3
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1612_01178_gb300 as ccl
@@ -717,7 +830,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve"], default="grid")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve", "ablation", "segsweep"],
+                    default="grid")
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serve: arrival rates (req/s)")
     ap.add_argument("--pool", type=int, default=128, help="serve: distinct request graphs")
@@ -739,7 +853,8 @@ def main(argv=None):
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    run = {"batched": run_batched, "serve": run_serve}.get(args.workload, run_ours)
+    run = {"batched": run_batched, "serve": run_serve, "ablation": run_ablation,
+           "segsweep": run_segsweep}.get(args.workload, run_ours)
     if world > 1:
         import torch
         import torch.distributed as dist

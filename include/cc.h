@@ -82,7 +82,13 @@ enum {
 typedef enum cc_mode {
   CC_MODE_AUTO = 0,        /* choose per graph size (currently: persistent) */
   CC_MODE_PERSISTENT = 1,  /* one cooperative launch; phases separated by grid barriers */
-  CC_MODE_MULTI_LAUNCH = 2 /* Fig. 4 as printed: one init, then Hook and Multi-Jump kernels per segment */
+  CC_MODE_MULTI_LAUNCH = 2, /* Fig. 4 as printed: one init, then Hook and Multi-Jump kernels per segment */
+  /* The baselines the paper measures against (Section IV, Fig. 5), CSR only: the host loop of
+     Fig. 1 with the non-atomic Hook and the single Jump of Fig. 2, reading a device change flag
+     after every Hook round and every Jump (one CPU-GPU round trip each) ... */
+  CC_MODE_SOMAN = 3,
+  /* ... and the same loop with each Compress done by one Multi-Jump launch. */
+  CC_MODE_SOMAN_MULTIJUMP = 4
 } cc_mode;
 
 typedef struct cc_options {
@@ -208,6 +214,8 @@ typedef struct cc_run_info {
   int32_t launches;    /* kernel launches issued by the call */
   int32_t tile_vertices; /* window of the hierarchical hook (0 = plain hook) */
   int64_t worklist_capacity; /* pairs the worklist could hold (hierarchical hook) */
+  int32_t host_round_trips;  /* device-to-host flag reads that decided convergence (Soman modes) */
+  int32_t hook_rounds;       /* Hook rounds of the host loop (Soman modes) */
 } cc_run_info;
 
 /* Worklist of the last hierarchical-hook launch: waits for the context's stream, then

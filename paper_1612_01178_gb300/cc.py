@@ -37,6 +37,8 @@ CC_FLAG_PHASE_TIMES = 8
 CC_MODE_AUTO = 0
 CC_MODE_PERSISTENT = 1
 CC_MODE_MULTI_LAUNCH = 2
+CC_MODE_SOMAN = 3
+CC_MODE_SOMAN_MULTIJUMP = 4
 
 CC_INDEX_I32 = 4
 CC_INDEX_I64 = 8
@@ -65,6 +67,8 @@ class cc_run_info(ctypes.Structure):
         ("launches", ctypes.c_int32),
         ("tile_vertices", ctypes.c_int32),
         ("worklist_capacity", ctypes.c_int64),
+        ("host_round_trips", ctypes.c_int32),
+        ("hook_rounds", ctypes.c_int32),
     ]
 
 

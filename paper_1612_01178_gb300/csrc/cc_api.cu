@@ -130,7 +130,7 @@ cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out) {
 }
 
 bool options_ok(const cc_options* o) {
-  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_MULTI_LAUNCH) return false;
+  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_SOMAN_MULTIJUMP) return false;
   if (o->segments < 0 || o->grid_blocks < 0) return false;
   if (o->chunk_arcs < -1 || (o->chunk_arcs > 0 && o->chunk_arcs % 32 != 0)) return false;
   if (o->tile_vertices != 0 && o->tile_vertices != -1 &&
@@ -182,6 +182,60 @@ cudaError_t grow_buffer(T** buf, size_t* have, size_t n) {
   }
   *have = n;
   return cudaSuccess;
+}
+
+// Reads DevStatus::changed after zeroing it and running `launch` (one CPU-GPU round trip).
+template <typename F>
+cc_status flag_round(cc_ctx* ctx, F&& launch, bool* changed, cc_run_info* info) {
+  cudaError_t e = cudaMemsetAsync(&ctx->d_status->changed, 0, sizeof(unsigned int), ctx->stream);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(cc::DevStatus), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host loop");
+  info->launches += 1;
+  info->host_round_trips += 1;
+  if (ctx->h_status->error != 0) return read_and_clear_status(ctx);
+  *changed = ctx->h_status->changed != 0;
+  return CC_OK;
+}
+
+// Fig. 1 driven from the host: repeat { Hook all arcs; Compress } until the Hook changes
+// nothing. Compress is a single Jump repeated until it changes nothing, or one Multi-Jump.
+cc_status run_host_loop(cc_ctx* ctx, const cc::Problem& p, const cc::Ctl& c, cc::LaunchShape s, bool multijump,
+                        cc_run_info* info) {
+  cudaError_t e = cc::launch_init_only(p, c, s, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "init launch");
+  info->launches += 1;
+  const long long guard = 2LL * p.V + 64;
+  for (long long round = 0;; ++round) {
+    if (round > guard) {
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error), "host loop did not converge");
+      return CC_ERR_INTERNAL;
+    }
+    bool hooked = false;
+    cc_status st = flag_round(ctx, [&] { return cc::launch_hook_nonatomic(p, c, s, ctx->stream); }, &hooked, info);
+    if (st != CC_OK) return st;
+    info->hook_rounds += 1;
+    if (!hooked) break;
+    if (multijump) {
+      e = cc::launch_jump_multi(p, c, s, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "multi-jump launch");
+      info->launches += 1;
+    } else {
+      for (long long j = 0;; ++j) {
+        if (j > guard) {
+          std::snprintf(ctx->last_error, sizeof(ctx->last_error), "jump loop did not converge");
+          return CC_ERR_INTERNAL;
+        }
+        bool jumped = false;
+        st = flag_round(ctx, [&] { return cc::launch_jump_single(p, c, s, ctx->stream); }, &jumped, info);
+        if (st != CC_OK) return st;
+        if (!jumped) break;
+      }
+    }
+  }
+  return CC_OK;
 }
 
 // Runs one single-graph problem on the context's stream.
@@ -281,6 +335,15 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
     info.grid_blocks = s.grid;
     info.launches += 1;
+  } else if (mode == CC_MODE_SOMAN || mode == CC_MODE_SOMAN_MULTIJUMP) {
+    if (p.kind != cc::kKindCsr) return CC_ERR_INVALID_ARG;
+    const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
+    const long long cap = (long long)per_sm * ctx->num_sms;
+    long long grid = o.grid_blocks > 0 ? o.grid_blocks : std::min(want, cap);
+    cc::LaunchShape s{(int)grid, block};
+    const cc_status st = run_host_loop(ctx, p, c, s, mode == CC_MODE_SOMAN_MULTIJUMP, &info);
+    if (st != CC_OK) return st;
+    info.grid_blocks = s.grid;
   } else {
     const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
     const long long cap = (long long)per_sm * ctx->num_sms;

@@ -24,7 +24,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct DevStatus {
   // per-launch fields (zeroed before every launch)
   unsigned int bar;
-  unsigned int pad0;
+  unsigned int changed;  // change flag of the host-driven modes (Fig. 1)
   unsigned long long counters[4];  // [0],[1] work counters; [2] worklist cursor; [3] overflowed units
   unsigned long long report[2];    // [0] worklist pairs, [1] worklist segments (hierarchical hook)
   // sticky error fields (cleared when the host reads them)
@@ -331,6 +331,21 @@ __device__ __forceinline__ void multi_jump(int* pi, int V, long long tid, long l
   }
 }
 
+// One Jump of Fig. 2 over every vertex: pi(v) <- pi(pi(v)); sets `changed` if any value moved.
+__device__ __forceinline__ void single_jump(int* pi, int V, long long tid, long long nthreads, const Ctl& c) {
+  bool ch = false;
+  for (long long vv = tid; vv < V; vv += nthreads) {
+    const int v = (int)vv;
+    const int p = ld_pi(pi + v);
+    const int g = ld_pi(pi + p);
+    if (g != p) {
+      st_pi(pi + v, g);
+      ch = true;
+    }
+  }
+  if (__ballot_sync(kFull, ch) && (threadIdx.x & 31) == 0) c.st->changed = 1u;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Segments and partitions: part i of n equal parts of [0, len).
 template <typename T>
@@ -479,7 +494,13 @@ __device__ __forceinline__ void sink_push(WarpSink& s, bool take, int u, int v, 
 // hooked on the shared-memory parent array lp; any other arc goes to the worklist through the
 // warp's sink. Otherwise every arc is Atomic-Hooked on pi, K at a time.
 // lo_row is a row with rp[lo_row] <= t0.
-template <typename OffT, bool SYM, bool TILED, int K>
+// How hook_csr_range joins an arc's trees.
+enum HookKind : int {
+  kHookAtomic = 0,    // Atomic-Hook (Fig. 3, top)
+  kHookNonAtomic = 1  // Hook of Fig. 2: pi(max(pi(u), pi(v))) <- min(...), plain store, sets `changed`
+};
+
+template <typename OffT, bool SYM, bool TILED, int K, int HOOK = kHookAtomic>
 __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                                int V, OffT t0, OffT t1, const Ctl& c, int lo_row,
                                                int* lp = nullptr, int wbase = 0, int W = 0,
@@ -535,6 +556,22 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         if (local) local_hook(lp, u[j] - wbase, v[j] - wbase);
         sink_push(*sink, live[j] && !local, u[j], v[j], c, ovf);
       }
+    } else if (HOOK == kHookNonAtomic) {
+      // Fig. 2: every tree is a star when a Hook round starts (the Compress before it ran to the
+      // end), so pi(u) and pi(v) are roots; the larger is pointed at the smaller with a plain store.
+      // Concurrent stores to one root may overwrite each other; the round then reports a change
+      // and the host repeats it (Fig. 1), which is why this hook needs no atomics.
+      bool ch = false;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (!live[j]) continue;
+        const int pu = ld_pi(pi + u[j]), pv = ld_pi(pi + v[j]);
+        if (pu != pv) {
+          st_pi(pi + (pu > pv ? pu : pv), pu > pv ? pv : pu);
+          ch = true;
+        }
+      }
+      if (__ballot_sync(kFull, ch) && lane == 0) c.st->changed = 1u;
     } else {
       if (vbase != 0) {  // graph of a batch: hook global IDs
 #pragma unroll
@@ -556,7 +593,7 @@ constexpr int kPairK = 4;   // worklist pairs per thread per step of phase B
 // c.chunk_arcs > 0, warps take chunks of that many arcs from the work counter `ctr` (zeroed
 // before the phase) until the segment is exhausted; otherwise each warp takes one fixed
 // contiguous slice.
-template <typename OffT, bool SYM>
+template <typename OffT, bool SYM, int HOOK = kHookAtomic>
 __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                               int V, OffT a0, OffT a1, long long tid, long long nthreads,
                                               unsigned long long* ctr, const Ctl& c) {
@@ -566,7 +603,7 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     const long long warp = tid >> 5, nwarps = nthreads >> 5;
     const OffT t0 = a0 + split_point<OffT>(len, nwarps, warp);
     const OffT t1 = a0 + split_point<OffT>(len, nwarps, warp + 1);
-    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, 0);
+    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
     return;
   }
   const OffT C = (OffT)c.chunk_arcs;
@@ -579,7 +616,7 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     if (t >= n_chunks) break;
     const OffT t0 = a0 + (OffT)t * C;
     const OffT t1 = (len - (OffT)t * C) > C ? t0 + C : a1;
-    hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, 0);
+    hook_csr_range<OffT, SYM, false, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
   }
 }
 

@@ -83,6 +83,15 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
 // out[1] += sampled arcs (out must be zeroed by the caller).
 cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* out, int threads, cudaStream_t stream);
 
+// Kernels of the host-driven loop of Fig. 1 (Soman et al.'s Hook-Compress with the Hook and
+// Jump of Fig. 2), kept for the ablation of Section IV: pi init; one non-atomic Hook round over
+// all arcs; one single Jump over all vertices; one Multi-Jump over all vertices. The Hook and
+// Jump rounds set DevStatus::changed.
+cudaError_t launch_init_only(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+cudaError_t launch_hook_nonatomic(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+cudaError_t launch_jump_single(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+cudaError_t launch_jump_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+
 // Device checks of CSR offsets and endpoints (CC_FLAG_VALIDATE).
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 

@@ -133,6 +133,19 @@ __global__ void __launch_bounds__(kMaxBlock) k_hook_coo(const int* __restrict__ 
   hook_coo_edges(src, dst, pi, V, e0, e1, global_tid(), global_threads(), c);
 }
 
+template <typename OffT, bool SYM>
+__global__ void __launch_bounds__(kMaxBlock) k_hook_csr_nonatomic(const OffT* __restrict__ rp,
+                                                                  const int* __restrict__ col, int* pi, int V, OffT nnz,
+                                                                  Ctl c) {
+  if (ld_relaxed(&c.st->error) != 0) return;
+  hook_csr_arcs<OffT, SYM, kHookNonAtomic>(rp, col, pi, V, (OffT)0, nnz, global_tid(), global_threads(), nullptr, c);
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k_jump_single(int* pi, int V, Ctl c) {
+  if (ld_relaxed(&c.st->error) != 0) return;
+  single_jump(pi, V, global_tid(), global_threads(), c);
+}
+
 __global__ void __launch_bounds__(kMaxBlock) k_jump(int* pi, int V, Ctl c) {
   if (global_tid() == 0) c.st->counters[0] = 0ull;
   if (ld_relaxed(&c.st->error) != 0) return;
@@ -307,6 +320,31 @@ cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* 
                          p.V, (long long)p.m, W, out);
   return launch_kernel(k_sample_locality<int>, s, 0, false, stream, static_cast<const int*>(p.rp), p.col, p.V, (int)p.m,
                        W, out);
+}
+
+cudaError_t launch_init_only(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
+  return launch_kernel(k_init, s, 0, false, stream, p.pi, p.V, c);
+}
+
+cudaError_t launch_hook_nonatomic(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
+  if (p.rp64) {
+    const long long* rp = static_cast<const long long*>(p.rp);
+    return p.sym ? launch_kernel(k_hook_csr_nonatomic<long long, true>, s, 0, false, stream, rp, p.col, p.pi, p.V,
+                                 (long long)p.m, c)
+                 : launch_kernel(k_hook_csr_nonatomic<long long, false>, s, 0, false, stream, rp, p.col, p.pi, p.V,
+                                 (long long)p.m, c);
+  }
+  const int* rp = static_cast<const int*>(p.rp);
+  return p.sym ? launch_kernel(k_hook_csr_nonatomic<int, true>, s, 0, false, stream, rp, p.col, p.pi, p.V, (int)p.m, c)
+               : launch_kernel(k_hook_csr_nonatomic<int, false>, s, 0, false, stream, rp, p.col, p.pi, p.V, (int)p.m, c);
+}
+
+cudaError_t launch_jump_single(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
+  return launch_kernel(k_jump_single, s, 0, false, stream, p.pi, p.V, c);
+}
+
+cudaError_t launch_jump_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
+  return launch_kernel(k_jump, s, 0, false, stream, p.pi, p.V, c);
 }
 
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {

@@ -323,3 +323,41 @@ def test_barrier_wait_times_out_and_context_survives(dev):
         out = cc.csr(rp, cl)  # hook disarmed itself; status cleared
         cc.sync()
         assert_labels(out.cpu().numpy(), want, "after timeout")
+
+
+# ------------------------------------------------------------------ the paper's baselines (Fig. 1/2)
+
+SOMAN = {"soman": ccapi.CC_MODE_SOMAN, "soman_multijump": ccapi.CC_MODE_SOMAN_MULTIJUMP}
+
+
+def gpu_csr_mode(dev, row_ptr, col, mode, sym=True):
+    flags = ccl.CC_FLAG_SYNC | (ccl.CC_FLAG_SYMMETRIC if sym else 0)
+    with ccl.ConnectedComponents(0, mode=mode, flags=flags) as cc:
+        out = cc.csr(torch.from_numpy(np.ascontiguousarray(row_ptr)).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(col, np.int32)).to(dev))
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), cc.run_info()
+
+
+@pytest.mark.parametrize("name", sorted(SOMAN))
+def test_host_driven_baselines(dev, name):
+    mode = SOMAN[name]
+    V, s, d = union_of_all_small_graphs()
+    for sym in (True, False):
+        rp, col = symmetric_csr(V, s, d, np.int32)
+        got, _ = gpu_csr_mode(dev, rp, col, mode, sym)
+        assert_labels(got, expect(rp, col), f"{name} small sym={sym}")
+    n = 100_000
+    for shape in (path_edges(range(n - 1, -1, -1)), path_edges(np.random.default_rng(1).permutation(n)),
+                  (np.full(n - 1, n - 1), np.arange(n - 1))):
+        rp, col = symmetric_csr(n, *shape, np.int32)
+        got, info = gpu_csr_mode(dev, rp, col, mode)
+        assert_labels(got, expect(rp, col), f"{name} adversarial")
+        assert info["host_round_trips"] >= info["hook_rounds"] >= 1
+    for g in (gen.workload_er_100k(), gen.grid_csr(1000, 0.6, seed=3), gen.rmat_csr(16, 8, seed=4)):
+        got, info = gpu_csr_mode(dev, g.row_ptr, g.col, mode)
+        assert_labels(got, expect(g.row_ptr, g.col), f"{name} {g}")
+    with ccl.ConnectedComponents(0, mode=mode, flags=ccl.CC_FLAG_SYNC) as cc:
+        s_ = torch.tensor([0], dtype=torch.int32, device=dev)
+        with pytest.raises(ccl.CCError):
+            cc.coo(2, s_, s_)  # the host-driven baselines take CSR input only

@@ -591,7 +591,8 @@ def run_ablation(args, rank, world, local_rank):
         ("Soman et al. (Fig. 1 + Fig. 2 Hook/Jump, host loop)", dict(mode=ccl.cc.CC_MODE_SOMAN)),
         ("+ Multi-Jump", dict(mode=ccl.cc.CC_MODE_SOMAN_MULTIJUMP)),
         ("+ Atomic-Hook, s = 1 (Fig. 4 host loop)", dict(mode=ccl.CC_MODE_MULTI_LAUNCH, segments=1, tile_vertices=-1)),
-        ("+ adaptive s = 2|E|/|V| (Fig. 4 host loop)", dict(mode=ccl.CC_MODE_MULTI_LAUNCH, tile_vertices=-1)),
+        ("+ adaptive s = 2|E|/|V| (Fig. 4 host loop)",
+         dict(mode=ccl.CC_MODE_MULTI_LAUNCH, tile_vertices=-1, segments=-1)),
         ("GB300 default (persistent, automatic hook)", dict()),
     ]
     rows = []

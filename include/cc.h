@@ -93,7 +93,10 @@ typedef enum cc_mode {
 
 typedef struct cc_options {
   int32_t mode;        /* cc_mode */
-  int32_t segments;    /* s; 0 = max(1, round(n_arcs / n_vertices)) (Section III-B; n_arcs = 2|E|) */
+  int32_t segments;    /* s of Fig. 4. -1 = the paper's s = max(1, round(2|E| / |V|)) (Section III-B;
+                          2|E| = n_arcs). 0 = this library's default from the same sweep on GB300:
+                          s = 4 when 2|E|/|V| < 3, else s = 1 (the two-phase hook splits its
+                          worklist E' into max(1, round(2|E'|/|V|)) segments). > 0 = exactly s. */
   int32_t block;       /* threads per block (a multiple of 32, at most 1024); 0 = 256 for the
                           plain hook and 1024 for the two-phase hook. A block that cannot be
                           co-resident is halved until it can. */

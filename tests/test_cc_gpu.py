@@ -361,3 +361,21 @@ def test_host_driven_baselines(dev, name):
         s_ = torch.tensor([0], dtype=torch.int32, device=dev)
         with pytest.raises(ccl.CCError):
             cc.coo(2, s_, s_)  # the host-driven baselines take CSR input only
+
+
+@pytest.mark.slow
+def test_rmat26_full_size(dev):
+    """R-MAT scale 26, edge factor 16 (2^31 arcs, int64 row offsets): full-size labels against the
+    oracle, in the launch configuration the benchmark uses (automatic choice, CC_FLAG_SYMMETRIC)."""
+    g = gen.workload_rmat_26()
+    assert g.row_ptr.dtype == np.int64 and g.nnz == 1 << 31
+    want = expect(g.row_ptr, g.col)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    for opts in (dict(), dict(segments=4)):
+        with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYMMETRIC | ccl.CC_FLAG_SYNC, **opts) as cc:
+            got = cc.csr(rp, col).cpu().numpy()
+        assert_labels(got, want, f"rmat26 {opts}")
+    n_comp = int((want == np.arange(g.n_vertices)).sum())
+    sizes = np.bincount(want)
+    assert sizes.max() > g.n_vertices // 4 and n_comp > 1000  # one giant component plus many singletons

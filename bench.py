@@ -48,6 +48,7 @@ WORKLOADS = {
     "er": ("er_V100000_E1000000", lambda: gen.workload_er_100k(seed=1)),
     "rmat": ("rmat26_ef16", lambda: gen.workload_rmat_26(seed=1)),
 }
+RMAT_SCALE = {"value": 26}  # --rmat-scale: smaller R-MAT graphs of the same family (profiling captures)
 
 
 def measured_peaks():
@@ -663,6 +664,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     name, make = WORKLOADS[args.workload]
+    if args.workload == "rmat" and args.rmat_scale != 26:
+        name = "rmat%d_ef16" % args.rmat_scale
+        make = lambda: gen.rmat_csr(args.rmat_scale, 16, seed=1, offsets64=True)  # noqa: E731
     t0 = time.perf_counter()
     g = make()
     gen_s = time.perf_counter() - t0
@@ -834,6 +838,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve", "ablation", "segsweep"],
                     default="grid")
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--rmat-scale", type=int, default=26, help="scale of the rmat workload (26 = the full size)")
     ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serve: arrival rates (req/s)")
     ap.add_argument("--pool", type=int, default=128, help="serve: distinct request graphs")
     ap.add_argument("--seconds", type=float, default=1.5, help="serve: arrival span per rate")

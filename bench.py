@@ -61,6 +61,22 @@ def measured_peaks():
         return DEFAULT_PEAK_GBS, "fallback"
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's); x itself at N = 1."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of N replicas that each process units_per_rank in (at most) ms_max."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def kernel_sources_sha256() -> str:
     """Hash of the CUDA sources, to tell whether recorded ncu counters still describe the kernel."""
     import glob
@@ -362,11 +378,7 @@ def run_batched(args, rank, world, local_rank):
     clocks = sampler.stop()
     cc.sync()
     ms = statistics.mean(step_ms)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
 
     # the same single-graph kernel run graph by graph (best per-graph hook choice, no sampling)
     rp_slices, col_slices, lab_slices, ctxs = [], [], [], {}
@@ -433,7 +445,7 @@ def run_batched(args, rank, world, local_rank):
     achieved = b_alg / (ms / 1000) / 1e9
     kinds = {k: b.kinds.count(k) for k in sorted(set(b.kinds))}
     line = {
-        "metric": "batched graphs/sec", "value": world * b.n_graphs / (ms_max / 1000), "unit": "graphs/s",
+        "metric": "batched graphs/sec", "value": job_rate(b.n_graphs, world, ms_max), "unit": "graphs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "batched%d" % b.n_graphs, "n_graphs": b.n_graphs, "total_vertices": b.total_vertices,
@@ -745,11 +757,7 @@ def run_ours(args, rank, world, local_rank):
     cc.sync()  # raises if any timed launch reported a device error
     step_ms = [a.elapsed_time(b) for a, b in events]
     ms = statistics.mean(step_ms)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     launches = info["launches"] * args.steps
 
     # end to end through the host-buffer entry point (pinned host inputs, labels read back)
@@ -770,11 +778,7 @@ def run_ours(args, rank, world, local_rank):
             t1 = time.perf_counter()
             cc_host.csr_host(pin_rp, pin_col, pin_out)
             tt.append(time.perf_counter() - t1)
-        e2e_s = statistics.mean(tt)
-        if dist is not None:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(statistics.mean(tt), dist)
         e2e_ok = np.array_equal(pin_out, gpu_labels)
         cc_host.close()
         e2e = {"value": world * g.n_edges / e2e_s, "unit": UNIT,
@@ -790,7 +794,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = b_alg / (ms / 1000) / 1e9
     line = {
         "metric": METRIC,
-        "value": world * g.n_edges / (ms_max / 1000),
+        "value": job_rate(g.n_edges, world, ms_max),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,

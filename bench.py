@@ -384,7 +384,7 @@ def run_batched(args, rank, world, local_rank):
     rp_slices, col_slices, lab_slices, ctxs = [], [], [], {}
     for kind in ("plain", "tiled"):
         ctxs[kind] = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags,
-                                             tile_vertices=-1 if kind == "plain" else 32768)
+                                             tile_vertices=-1 if kind == "plain" else 16384)
     for g in range(b.n_graphs):
         v0, v1, a0, a1 = int(b.v_off[g]), int(b.v_off[g + 1]), int(b.a_off[g]), int(b.a_off[g + 1])
         rp_slices.append(rp[v0 + g: v1 + g + 1])

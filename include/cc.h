@@ -112,7 +112,7 @@ typedef struct cc_options {
                           hooks on pi in s' = 2|E'|/|V| segments (or `segments` if set), each
                           followed by a Multi-Jump. -1 = off: every arc is hooked on pi (Fig. 4
                           as printed). 0 = automatic: graphs of at least 2^17 vertices whose
-                          sampled arcs mostly stay inside 32768-vertex windows use the two-phase
+                          sampled arcs mostly stay inside 16384-vertex windows use the two-phase
                           hook; the sample is a small kernel plus a synchronisation on the first
                           call for a given (row_ptr, col_idx, V, n_arcs), reused afterwards. */
   int32_t reserved;    /* must be 0 */

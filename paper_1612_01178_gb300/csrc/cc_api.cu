@@ -50,7 +50,11 @@ namespace {
 
 constexpr long long kDefaultTimeoutNs = 2000000000LL;
 constexpr int kDefaultChunkArcs = -1;
-constexpr int kDefaultTileVertices = 32768;
+// Default window of the two-phase hook: single graphs use 16384 vertices (64 KB of 32-bit local
+// parents, two 1024-thread CTAs per SM); the batched kernel keeps whole graphs of up to 32768
+// vertices in one CTA.
+constexpr int kDefaultTileVertices = 16384;
+constexpr int kBatchedTileVertices = 32768;
 constexpr int kMaxTileVertices = 32768;
 constexpr int kPlainBlock = 256;   // default block of the plain hook
 constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
@@ -344,10 +348,25 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     } else {
       ctx->phase_valid = false;
     }
-    if (e == cudaSuccess) e = cc::launch_persistent(p, c, s, ctx->stream);
+    if (e == cudaSuccess && p.tile_w > 0) {
+      // Phase A: one CTA per window at most, as many as are co-resident.
+      int block_a = o.block > 0 ? o.block : kTiledBlock;
+      int per_sm_a = cc::phase_a_blocks_per_sm(p, block_a);
+      while (per_sm_a <= 0 && block_a > 32) {
+        block_a /= 2;
+        per_sm_a = cc::phase_a_blocks_per_sm(p, block_a);
+      }
+      if (per_sm_a <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "phase A occupancy");
+      const long long n_units = (p.V + p.tile_w - 1) / p.tile_w;
+      const long long grid_a = std::min<long long>(n_units, (long long)per_sm_a * ctx->num_sms);
+      e = cc::launch_two_phase(p, c, cc::LaunchShape{(int)grid_a, block_a}, s, ctx->stream);
+      info.launches += 2;
+    } else if (e == cudaSuccess) {
+      e = cc::launch_persistent(p, c, s, ctx->stream);
+      info.launches += 1;
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
     info.grid_blocks = s.grid;
-    info.launches += 1;
   } else if (mode == CC_MODE_SOMAN || mode == CC_MODE_SOMAN_MULTIJUMP) {
     if (p.kind != cc::kKindCsr) return CC_ERR_INVALID_ARG;
     const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
@@ -519,7 +538,7 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   const cc_options& o = ctx->opt;
   const int n_graphs = p.n_graphs;
   const long long total_vertices = p.total_v;
-  const int W = o.tile_vertices > 0 ? window_for(INT32_MAX, o.tile_vertices) : kDefaultTileVertices;
+  const int W = o.tile_vertices > 0 ? window_for(INT32_MAX, o.tile_vertices) : kBatchedTileVertices;
   int block = o.block > 0 ? o.block : kTiledBlock;
   const bool sym = (o.flags & CC_FLAG_SYMMETRIC) != 0;
   int per_sm = cc::batched_blocks_per_sm(sym, block, W);

@@ -191,8 +191,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   // Phase A over all windows of all graphs.
   int* lp = smem;
   WarpSink sink;
-  sink.buf = reinterpret_cast<int2*>(smem + W) + (threadIdx.x >> 5) * kSinkPairs;
-  sink.count = 0;
+  warp_scratch_init(sink, reinterpret_cast<unsigned char*>(smem + W));
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = atomicAdd(&c.st->counters[0], 1ull);
@@ -226,7 +225,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       }
     } else {
       if (ui.nnz <= 0x7fffffffLL)
-        phase_a_window<int, SYM>(ui.rp, ui.col, ui.vg, (int)ui.nnz, ui.w0, ui.nrows, ui.vbase, lp, sink, &s_ovf,
+        phase_a_window<int, SYM, int>(ui.rp, ui.col, ui.vg, (int)ui.nnz, ui.w0, ui.nrows, ui.vbase, lp, sink, &s_ovf,
                                  &s_bad, c);
       else
         __syncthreads();
@@ -258,25 +257,11 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     c.st->report[0] = n_pairs;
     c.st->report[1] = (unsigned long long)s2;
   }
-  constexpr int K = kPairK;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (long long seg = 0; seg < s2; ++seg) {
     const unsigned long long p0 = split_point<unsigned long long>(n_pairs, s2, seg);
     const unsigned long long p1 = split_point<unsigned long long>(n_pairs, s2, seg + 1);
-    const unsigned long long T = (unsigned long long)nt;
-    for (unsigned long long base = p0 + (unsigned long long)tid; base < p1; base += T * K) {
-      int u[K], v[K];
-      bool live[K];
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const unsigned long long i = base + (unsigned long long)j * T;
-        live[j] = i < p1;
-        const int2 e = live[j] ? c.wl[i] : make_int2(0, 0);
-        u[j] = e.x;
-        v[j] = e.y;
-      }
-      atomic_hook_k<K>(b.labels, u, v, live, b.total_v, c);
-    }
+    hook_worklist(b.labels, c.wl, p0, p1, tid, nt, b.total_v, c);
     if (seg == 0) {  // windows without locality: every arc on pi, each window split over `parts` CTAs
       const unsigned long long parts = split_factor(n_plain, gridDim.x);
       for (unsigned long long item = blockIdx.x; item < n_plain * parts; item += gridDim.x) {
@@ -293,8 +278,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
           const int t0 = a0 + split_point<int>(a1 - a0, nwarps, warp);
           const int t1 = a0 + split_point<int>(a1 - a0, nwarps, warp + 1);
           if (t0 < t1)
-            hook_csr_range<int, SYM, false, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, nullptr, 0, 0,
-                                                    nullptr, nullptr, ui.vbase, &s_bad);
+            hook_csr_range<int, SYM, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, ui.vbase, &s_bad);
         } else if (threadIdx.x == 0) {
           raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
           s_bad = 1;

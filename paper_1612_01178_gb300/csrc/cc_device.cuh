@@ -63,6 +63,7 @@ struct Ctl {
   int window_mode = 0;                    // batched: kWindowsSampled or kWindowsPlain
   unsigned long long* phase_ns = nullptr; // optional per-barrier timestamps (block 0)
   int phase_cap = 0;
+  int phase_off = 0;                      // slot of the first barrier's timestamp, minus one
 };
 
 // How the batched kernel hooks windows of multi-window graphs.
@@ -158,7 +159,8 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
     }
     if (go && ld_relaxed(&c.st->error) != 0) go = 0;
     __threadfence();
-    if (c.phase_ns && blockIdx.x == 0 && (int)epoch < c.phase_cap - 1) c.phase_ns[epoch] = now_ns();
+    if (c.phase_ns && blockIdx.x == 0 && (int)epoch + c.phase_off < c.phase_cap - 1)
+      c.phase_ns[epoch + c.phase_off] = now_ns();
     s_go = go;
   }
   __syncthreads();
@@ -231,7 +233,10 @@ __device__ __forceinline__ int root_from2(int* pi, int a, int pa, int ga) {
 // are loaded together and all first CASes are issued together, so a thread keeps up to 2K
 // loads or K atomics in flight instead of one dependent chain; deeper walks and failed CASes
 // then finish one edge at a time exactly as in atomic_hook.
-template <int K>
+// DEDUP (the whole warp must call, converged): lanes whose edge j found the same pair of roots
+// (H, L) leave it to the lowest such lane, whose hook joins exactly those two trees; this keeps
+// thousands of CASes off one root when many edges join the same two components.
+template <int K, bool DEDUP = false>
 __device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const int (&v)[K], const bool (&live)[K],
                                               int V, const Ctl& c) {
   int pu[K], pv[K];
@@ -256,6 +261,16 @@ __device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const 
     if (ru == rv) continue;
     H[j] = ru > rv ? ru : rv;
     L[j] = ru > rv ? rv : ru;
+  }
+  if (DEDUP) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const unsigned long long key =
+          H[j] >= 0 ? (((unsigned long long)(unsigned)H[j] << 32) | (unsigned)L[j]) : ~0ull;
+      const unsigned grp = __match_any_sync(kFull, key);
+      if (H[j] >= 0 && lane != __ffs(grp) - 1) H[j] = -1;
+    }
   }
 #pragma unroll
   for (int j = 0; j < K; ++j)
@@ -303,23 +318,62 @@ __device__ __forceinline__ int4 ld_pi4(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ void st_pi4(int* p, int4 v) {
+  asm volatile("st.global.v4.s32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+
+// Jump of four consecutive vertices v..v+3 whose parents p were loaded: the grandparents g and
+// great-grandparents h of all four are loaded together. A vertex whose grandparent is a root
+// (h == g) ends at g; the four results go out in one 16-byte store when any moved. Deeper walks
+// continue one step at a time, writing every step.
+struct Jump4 {
+  int4 p, g, h;
+};
+
+__device__ __forceinline__ int jump_gather(int* pi, int v, int p) { return p != v ? ld_pi(pi + p) : p; }
+
+__device__ __forceinline__ void jump4_load(int* pi, int v, Jump4& s) {
+  s.p = ld_pi4(pi + v);
+}
+__device__ __forceinline__ void jump4_level2(int* pi, int v, Jump4& s) {
+  s.g = make_int4(jump_gather(pi, v, s.p.x), jump_gather(pi, v + 1, s.p.y), jump_gather(pi, v + 2, s.p.z),
+                  jump_gather(pi, v + 3, s.p.w));
+}
+__device__ __forceinline__ void jump4_level3(int* pi, Jump4& s) {
+  s.h = make_int4(jump_gather(pi, s.p.x, s.g.x), jump_gather(pi, s.p.y, s.g.y), jump_gather(pi, s.p.z, s.g.z),
+                  jump_gather(pi, s.p.w, s.g.w));
+}
+__device__ __forceinline__ void jump4_finish(int* pi, int v, const Jump4& s, int V, const Ctl& c) {
+  if (s.g.x != s.p.x || s.g.y != s.p.y || s.g.z != s.p.z || s.g.w != s.p.w) {
+    st_pi4(pi + v, s.g);
+    if (s.h.x != s.g.x) jump_from(pi, v, s.g.x, s.h.x, V, c);
+    if (s.h.y != s.g.y) jump_from(pi, v + 1, s.g.y, s.h.y, V, c);
+    if (s.h.z != s.g.z) jump_from(pi, v + 2, s.g.z, s.h.z, V, c);
+    if (s.h.w != s.g.w) jump_from(pi, v + 3, s.g.w, s.h.w, V, c);
+  }
+}
+
 __device__ __forceinline__ void multi_jump(int* pi, int V, long long tid, long long nthreads, const Ctl& c) {
   long long first_scalar = 0;
   if ((reinterpret_cast<uintptr_t>(pi) & 15) == 0) {
-    // Four consecutive vertices per thread: one 16-byte load of pi(v..v+3), then their four
-    // grandparent loads issued together before any of the (rare) longer walks.
+    // Two groups of four consecutive vertices per thread and step (groups q and q + T): their
+    // 16-byte parent loads, then the grandparent and great-grandparent gathers of all eight are
+    // issued level by level, so each thread keeps eight walks in flight.
     const long long n4 = V >> 2;
-    for (long long q = tid; q < n4; q += nthreads) {
-      const int v = (int)(q << 2);
-      const int4 p = ld_pi4(pi + v);
-      const int g0 = p.x != v ? ld_pi(pi + p.x) : p.x;
-      const int g1 = p.y != v + 1 ? ld_pi(pi + p.y) : p.y;
-      const int g2 = p.z != v + 2 ? ld_pi(pi + p.z) : p.z;
-      const int g3 = p.w != v + 3 ? ld_pi(pi + p.w) : p.w;
-      if (g0 != p.x) jump_from(pi, v, p.x, g0, V, c);
-      if (g1 != p.y) jump_from(pi, v + 1, p.y, g1, V, c);
-      if (g2 != p.z) jump_from(pi, v + 2, p.z, g2, V, c);
-      if (g3 != p.w) jump_from(pi, v + 3, p.w, g3, V, c);
+    for (long long q = tid; q < n4; q += 2 * nthreads) {
+      const long long q2 = q + nthreads;
+      const bool two = q2 < n4;
+      const int v = (int)(q << 2), v2 = two ? (int)(q2 << 2) : v;
+      Jump4 a, b;
+      jump4_load(pi, v, a);
+      if (two) jump4_load(pi, v2, b);
+      else b.p = make_int4(v, v + 1, v + 2, v + 3);
+      jump4_level2(pi, v, a);
+      jump4_level2(pi, v2, b);
+      jump4_level3(pi, a);
+      jump4_level3(pi, b);
+      jump4_finish(pi, v, a, V, c);
+      if (two) jump4_finish(pi, v2, b, V, c);
     }
     first_scalar = n4 << 2;
   }
@@ -376,28 +430,33 @@ __device__ __forceinline__ int warp_row_search(const OffT* rp, int lo, int hi, O
   return lo + (31 - __clz(m));
 }
 
-// Root of x in a CTA-local parent array (shared memory), with path halving. The local array
-// obeys the same invariant as pi (lp(x) <= x), so the walk ends within W steps.
-__device__ __forceinline__ int lfind(volatile int* lp, int x) {
+// Root of x in a CTA-local parent array (shared memory), with path halving. The local array obeys the same invariant as pi (lp(x) <= x), so the walk ends
+// within W steps.
+template <typename LT>
+__device__ __forceinline__ int lfind(volatile LT* lp, int x) {
   int px = lp[x];
   while (px != x) {
     const int gx = lp[px];
     if (gx == px) return px;
-    lp[x] = gx;
+    lp[x] = (LT)gx;
     x = gx;
     px = lp[x];
   }
   return x;
 }
 
-// Atomic-Hook of local indices (a, b) on the shared-memory parent array.
-__device__ __forceinline__ void local_hook(int* lp, int a, int b) {
-  volatile int* vlp = lp;
+__device__ __forceinline__ int cas_local(int* p, int cmp, int val) { return atomicCAS(p, cmp, val); }
+
+// Atomic-Hook of local indices (a, b) on the shared-memory parent array: both roots are found,
+// and the higher is CAS-linked to the lower until the CAS succeeds or the roots agree.
+template <typename LT>
+__device__ __forceinline__ void local_hook(LT* lp, int a, int b) {
+  volatile LT* vlp = lp;
   int ra = lfind(vlp, a), rb = lfind(vlp, b);
   while (ra != rb) {
     const int H = ra > rb ? ra : rb;
     const int L = ra > rb ? rb : ra;
-    const int old = atomicCAS(lp + H, H, L);
+    const int old = cas_local(lp + H, H, L);
     if (old == H) return;
     ra = lfind(vlp, old);
     rb = lfind(vlp, L);
@@ -454,13 +513,33 @@ __device__ __forceinline__ int resolve_row(const OffT* __restrict__ rp, int V, i
 // Per-warp staging buffer in shared memory for the worklist of the two-phase hook: arcs are
 // appended by ballot (no atomics) and flushed to the global worklist with one atomic per flush.
 constexpr int kSinkPairs = 128;
+// Local hooks that the fast path of phase A could not finish wait in a per-warp queue of
+// kDeferCap packed pairs (two 16-bit local indices) and are finished 32 at a time.
+constexpr int kDeferCap = 64;
+constexpr int kWarpScratchBytes = kSinkPairs * (int)sizeof(int2) + kDeferCap * (int)sizeof(unsigned);
+
+// Flags a warp gathers during phase A (reported to the CTA at the end of the window).
+constexpr int kSinkOverflow = 1;  // a worklist append did not fit
+constexpr int kSinkBadArc = 2;    // an arc endpoint was outside [0, V)
 
 struct WarpSink {
-  int2* buf;  // kSinkPairs entries in shared memory, private to the warp
-  int count;  // warp-uniform
+  int2* buf;   // kSinkPairs entries in shared memory, private to the warp, then kDeferCap
+               // deferred local hooks
+  int count;   // warp-uniform
+  int dcount;  // warp-uniform, < 32 between calls
+  int flags;   // kSinkOverflow | kSinkBadArc, per lane
+  __device__ __forceinline__ unsigned* dq() const { return reinterpret_cast<unsigned*>(buf + kSinkPairs); }
 };
 
-__device__ __forceinline__ void sink_flush(WarpSink& s, const Ctl& c, volatile int* ovf) {
+// Points s at the calling warp's part of the per-warp scratch that starts at `base`.
+__device__ __forceinline__ void warp_scratch_init(WarpSink& s, unsigned char* base) {
+  s.buf = reinterpret_cast<int2*>(base + (threadIdx.x >> 5) * kWarpScratchBytes);
+  s.count = 0;
+  s.dcount = 0;
+  s.flags = 0;
+}
+
+__device__ __forceinline__ void sink_flush(WarpSink& s, const Ctl& c) {
   if (s.count == 0) return;
   const int lane = threadIdx.x & 31;
   __syncwarp();
@@ -470,17 +549,71 @@ __device__ __forceinline__ void sink_flush(WarpSink& s, const Ctl& c, volatile i
   for (int i = lane; i < s.count; i += 32) {
     const unsigned long long pos = base + (unsigned long long)i;
     if (pos < c.wl_cap) c.wl[pos] = s.buf[i];
-    else *ovf = 1;
+    else s.flags |= kSinkOverflow;
   }
   __syncwarp();
   s.count = 0;
 }
 
-__device__ __forceinline__ void sink_push(WarpSink& s, bool take, int u, int v, const Ctl& c, volatile int* ovf) {
+// One step of the local hook of (a, b) that needs no root walk: done if a and b have the same
+// parent; else, if one of them is a root whose ID is above the other's parent, a CAS links it
+// to that parent (an ancestor of the other endpoint, so the invariant lp(x) <= x holds and the
+// two trees are joined). Returns false when the hook is left for local_hook.
+template <typename LT>
+__device__ __forceinline__ bool local_hook_try(LT* lp, int a, int b) {
+  const int pa = reinterpret_cast<volatile LT*>(lp)[a];
+  const int pb = reinterpret_cast<volatile LT*>(lp)[b];
+  if (pa == pb) return true;
+  int H, L;
+  if (pb == b && b > pa) {
+    H = b;
+    L = pa;
+  } else if (pa == a && a > pb) {
+    H = a;
+    L = pb;
+  } else {
+    return false;
+  }
+  return cas_local(lp + H, H, L) == H;
+}
+
+// Queues the hooks that local_hook_try left (lanes with `take`) and finishes 32 of them, one per
+// lane, whenever 32 are waiting, so the root walks run with every lane busy.
+template <typename LT>
+__device__ __forceinline__ void defer_push(WarpSink& s, bool take, int a, int b, LT* lp) {
+  const unsigned m = __ballot_sync(kFull, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  if (take) s.dq()[s.dcount + __popc(m & ((1u << lane) - 1u))] = (unsigned)a | ((unsigned)b << 16);
+  s.dcount += __popc(m);
+  if (s.dcount >= 32) {
+    __syncwarp();
+    const unsigned e = s.dq()[s.dcount - 32 + lane];
+    __syncwarp();
+    s.dcount -= 32;
+    local_hook(lp, (int)(e & 0xffffu), (int)(e >> 16));
+  }
+}
+
+// Finishes the hooks still queued (fewer than 32).
+template <typename LT>
+__device__ __forceinline__ void defer_drain(WarpSink& s, LT* lp) {
+  if (s.dcount == 0) return;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (lane < s.dcount) {
+    const unsigned e = s.dq()[lane];
+    local_hook(lp, (int)(e & 0xffffu), (int)(e >> 16));
+  }
+  __syncwarp();
+  s.dcount = 0;
+}
+
+__device__ __forceinline__ void sink_push(WarpSink& s, bool take, int u, int v, const Ctl& c) {
   const unsigned m = __ballot_sync(kFull, take);
   if (!m) return;
   const int n = __popc(m);
-  if (s.count + n > kSinkPairs) sink_flush(s, c, ovf);
+  if (s.count + n > kSinkPairs) sink_flush(s, c);
   const int lane = threadIdx.x & 31;
   if (take) s.buf[s.count + __popc(m & ((1u << lane) - 1u))] = make_int2(u, v);
   s.count += n;
@@ -489,23 +622,20 @@ __device__ __forceinline__ void sink_push(WarpSink& s, bool take, int u, int v, 
 // Atomic-Hook over the arcs [t0, t1) of a CSR graph by one warp, 32 x K arcs per step: lane l
 // takes arcs b + l + 32 j, j < K (each j a coalesced read of col_idx), and the next step's
 // arcs are loaded before the current ones are hooked, so the arc stream stays in flight.
-// SYM: the CSR holds both directions of every edge, so arcs with u > v are skipped.
-// TILED (phase A of the two-phase hook): an arc with both endpoints in [wbase, wbase + W) is
-// hooked on the shared-memory parent array lp; any other arc goes to the worklist through the
-// warp's sink. Otherwise every arc is Atomic-Hooked on pi, K at a time.
-// lo_row is a row with rp[lo_row] <= t0.
+// SYM: the CSR holds both directions of every edge, so arcs with u > v are skipped. Every arc
+// is Atomic-Hooked on pi, K at a time (or with the plain-store hook of Fig. 2). lo_row is a row
+// with rp[lo_row] <= t0; vbase is added to both endpoints (a graph of a batch) and `bad`
+// records an endpoint outside [0, V).
 // How hook_csr_range joins an arc's trees.
 enum HookKind : int {
   kHookAtomic = 0,    // Atomic-Hook (Fig. 3, top)
   kHookNonAtomic = 1  // Hook of Fig. 2: pi(max(pi(u), pi(v))) <- min(...), plain store, sets `changed`
 };
 
-template <typename OffT, bool SYM, bool TILED, int K, int HOOK = kHookAtomic>
+template <typename OffT, bool SYM, int K, int HOOK = kHookAtomic>
 __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
-                                               int V, OffT t0, OffT t1, const Ctl& c, int lo_row,
-                                               int* lp = nullptr, int wbase = 0, int W = 0,
-                                               WarpSink* sink = nullptr, volatile int* ovf = nullptr,
-                                               int vbase = 0, volatile int* bad = nullptr) {
+                                               int V, OffT t0, OffT t1, const Ctl& c, int lo_row, int vbase = 0,
+                                               volatile int* bad = nullptr) {
   const int lane = threadIdx.x & 31;
   int r = warp_row_search<OffT>(rp, lo_row, V, t0);
   int vn[K];
@@ -548,15 +678,7 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         }
       }
     }
-    if (TILED) {
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const bool local =
-            live[j] && (unsigned)(u[j] - wbase) < (unsigned)W && (unsigned)(v[j] - wbase) < (unsigned)W;
-        if (local) local_hook(lp, u[j] - wbase, v[j] - wbase);
-        sink_push(*sink, live[j] && !local, u[j], v[j], c, ovf);
-      }
-    } else if (HOOK == kHookNonAtomic) {
+    if (HOOK == kHookNonAtomic) {
       // Fig. 2: every tree is a star when a Hook round starts (the Compress before it ran to the
       // end), so pi(u) and pi(v) are roots; the larger is pointed at the smaller with a plain store.
       // Concurrent stores to one root may overwrite each other; the round then reports a change
@@ -583,7 +705,6 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
       atomic_hook_k<K>(pi, u, v, live, vbase + V, c);
     }
   }
-  if (TILED) sink_flush(*sink, c, ovf);
 }
 
 constexpr int kHookK = 1;   // arcs per lane per step of the plain hook
@@ -603,7 +724,7 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     const long long warp = tid >> 5, nwarps = nthreads >> 5;
     const OffT t0 = a0 + split_point<OffT>(len, nwarps, warp);
     const OffT t1 = a0 + split_point<OffT>(len, nwarps, warp + 1);
-    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+    if (t0 < t1) hook_csr_range<OffT, SYM, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
     return;
   }
   const OffT C = (OffT)c.chunk_arcs;
@@ -616,13 +737,16 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     if (t >= n_chunks) break;
     const OffT t0 = a0 + (OffT)t * C;
     const OffT t1 = (len - (OffT)t * C) > C ? t0 + C : a1;
-    hook_csr_range<OffT, SYM, false, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+    hook_csr_range<OffT, SYM, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
   }
 }
 
-// Bytes of dynamic shared memory of the two-phase hook for a block of `block` threads.
-__host__ __device__ __forceinline__ size_t tiled_smem_bytes(int W, int block) {
-  return (size_t)W * sizeof(int) + (size_t)(block / 32) * kSinkPairs * sizeof(int2);
+// Bytes of dynamic shared memory of phase A for a block of `block` threads: the window's parent
+// array (W entries of lt_bytes each) followed by the per-warp scratch (worklist sink and queue
+// of deferred local hooks).
+__host__ __device__ __forceinline__ size_t tiled_smem_bytes(int W, int block, int lt_bytes = (int)sizeof(int)) {
+  const size_t lp = ((size_t)W * (size_t)lt_bytes + 15) & ~(size_t)15;
+  return lp + (size_t)(block / 32) * kWarpScratchBytes;
 }
 
 // Rows with more arcs than this are walked by a whole warp in phase A.
@@ -667,19 +791,20 @@ __device__ __forceinline__ void load_group(const int* __restrict__ col, OffT x0,
 // Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window. IDs
 // are local to the graph (< V); worklist entries get vbase added (the graph's first vertex in a
 // batch). `bad` records an endpoint outside [0, V).
-template <bool SYM>
+template <bool SYM, typename LT>
 __device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, long long a, int V, int w0, int nrows,
-                                            int* lp, WarpSink& sink, volatile int* ovf, volatile int* bad, int vbase,
-                                            const Ctl& c) {
+                                            LT* lp, WarpSink& sink, int vbase, const Ctl& c) {
   const bool in_range = has && (unsigned)v < (unsigned)V;
   if (has && !in_range) {
     raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
-    *bad = 1;
+    sink.flags |= kSinkBadArc;
   }
   const bool live = in_range && (SYM ? (v > u) : (v != u));
-  const bool local = live && (unsigned)(v - w0) < (unsigned)nrows;
-  if (local) local_hook(lp, i, v - w0);
-  sink_push(sink, live && !local, u + vbase, v + vbase, c, ovf);
+  const int b = v - w0;
+  const bool local = live && (unsigned)b < (unsigned)nrows;
+  const bool left = local && !local_hook_try(lp, i, b);
+  defer_push(sink, left, i, b, lp);
+  sink_push(sink, live && !local, u + vbase, v + vbase, c);
 }
 
 // Phase A of one window [w0, w0 + nrows) of a graph with V vertices and nnz arcs (rows rp,
@@ -687,12 +812,11 @@ __device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, long 
 // must separate that from this call); on return (after a barrier) lp holds the window's local
 // forest. Warps take 32-row chunks (one row per lane) in an interleaved order, so the CTA sweeps
 // the window roughly in ID order and new vertices mostly join components that already have
-// short paths to their roots. Loads run ahead of the hooks: row offsets two chunks ahead, the
-// first kGroup arcs of each row one chunk ahead. Rows of more than kHeavyRow arcs are walked by
-// the whole warp, 32 arcs at a time.
-template <typename OffT, bool SYM>
+// short paths to their roots. Row offsets are loaded one chunk ahead. Rows of more than
+// kHeavyRow arcs are walked by the whole warp, 32 arcs at a time.
+template <typename OffT, bool SYM, typename LT>
 __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, const int* __restrict__ col, int V,
-                                               OffT nnz, int w0, int nrows, int vbase, int* lp, WarpSink& sink,
+                                               OffT nnz, int w0, int nrows, int vbase, LT* lp, WarpSink& sink,
                                                volatile int* ovf, volatile int* bad, const Ctl& c) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int step = nwarps * 32;
@@ -700,32 +824,29 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
   const int r_end = nrows;
   if (r_begin < r_end) {  // warp-uniform
     OffT a0, a1, na0, na1;
-    int v[kGroup], nv[kGroup];
-    load_row_span<OffT>(rp, w0, r_begin + lane, r_end, a0, a1);
-    check_span<OffT>(a0, a1, nnz, w0 + r_begin + lane, c);
-    load_group<OffT>(col, a0, a1, 0, v);
-    load_row_span<OffT>(rp, w0, r_begin + step + lane, r_end, na0, na1);
+    load_row_span<OffT>(rp, w0, r_begin + lane, r_end, na0, na1);
     for (int base = r_begin; base < r_end; base += step) {
-      check_span<OffT>(na0, na1, nnz, w0 + base + step + lane, c);
-      load_group<OffT>(col, na0, na1, 0, nv);
-      OffT nna0, nna1;
-      load_row_span<OffT>(rp, w0, base + 2 * step + lane, r_end, nna0, nna1);
+      a0 = na0;
+      a1 = na1;
+      check_span<OffT>(a0, a1, nnz, w0 + base + lane, c);
+      int v[kGroup];
+      load_group<OffT>(col, a0, a1, 0, v);
+      load_row_span<OffT>(rp, w0, base + step + lane, r_end, na0, na1);
       const int i = base + lane;
       const int u = w0 + i;
       const long long deg = (long long)(a1 - a0);
       const bool heavy = deg > kHeavyRow;
 #pragma unroll
       for (int j = 0; j < kGroup; ++j)
-        phase_a_arc<SYM>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, ovf, bad, vbase,
-                         c);
+        phase_a_arc<SYM, LT>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, vbase, c);
       const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
       for (int g = 1; g * kGroup < maxdeg; ++g) {
         int w[kGroup];
         load_group<OffT>(col, a0, heavy ? a0 : a1, g, w);
 #pragma unroll
         for (int j = 0; j < kGroup; ++j)
-          phase_a_arc<SYM>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0, nrows,
-                           lp, sink, ovf, bad, vbase, c);
+          phase_a_arc<SYM, LT>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0, nrows,
+                           lp, sink, vbase, c);
       }
       unsigned hv = __ballot_sync(kFull, heavy);
       while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
@@ -737,18 +858,16 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
           const OffT a = bb + lane;
           const bool has = a < h1;
           const int vv = has ? ld_stream(col + a) : 0;
-          phase_a_arc<SYM>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, ovf, bad, vbase, c);
+          phase_a_arc<SYM, LT>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, vbase, c);
         }
       }
-      a0 = na0;
-      a1 = na1;
-      na0 = nna0;
-      na1 = nna1;
-#pragma unroll
-      for (int j = 0; j < kGroup; ++j) v[j] = nv[j];
     }
   }
-  sink_flush(sink, c, ovf);
+  defer_drain(sink, lp);
+  sink_flush(sink, c);
+  if (sink.flags & kSinkOverflow) *ovf = 1;
+  if (sink.flags & kSinkBadArc) *bad = 1;
+  sink.flags = 0;
   __syncthreads();
 }
 
@@ -761,18 +880,18 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
 // window's part of pi with plain stores: pi(x) = w0 + local root of x, the minimum vertex of
 // x's local component. Every vertex belongs to exactly one window, so this also initialises
 // pi, and no two CTAs write the same entry. If the worklist is full, the window is recorded as
-// overflowed and phase B hooks all of its arcs again on pi.
-template <typename OffT, bool SYM>
+// overflowed and phase B hooks all of its arcs again on pi. LT is the type of the local parent
+// entries (a 32-bit shared-memory CAS must exist for it).
+template <typename OffT, bool SYM, typename LT>
 __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
-                                              int V, OffT nnz, int* smem, const Ctl& c) {
+                                              int V, OffT nnz, unsigned char* smem, const Ctl& c) {
   __shared__ unsigned long long s_unit;
   __shared__ int s_ovf, s_bad;
   const int W = c.tile_w;
-  int* lp = smem;
+  LT* lp = reinterpret_cast<LT*>(smem);
   const long long n_units = ((long long)V + W - 1) / W;
   WarpSink sink;
-  sink.buf = reinterpret_cast<int2*>(smem + W) + (threadIdx.x >> 5) * kSinkPairs;
-  sink.count = 0;
+  warp_scratch_init(sink, smem + (((size_t)W * sizeof(LT) + 15) & ~(size_t)15));
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = atomicAdd(&c.st->counters[0], 1ull);
@@ -784,10 +903,10 @@ __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const
     if (k >= (unsigned long long)n_units) break;
     const int w0 = (int)(k * (unsigned long long)W);
     const int nrows = (V - w0) < W ? (V - w0) : W;
-    for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = i;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = (LT)i;
     __syncthreads();
-    phase_a_window<OffT, SYM>(rp, col, V, nnz, w0, nrows, 0, lp, sink, &s_ovf, &s_bad, c);
-    volatile int* vlp = lp;
+    phase_a_window<OffT, SYM, LT>(rp, col, V, nnz, w0, nrows, 0, lp, sink, &s_ovf, &s_bad, c);
+    volatile LT* vlp = lp;
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) pi[w0 + i] = w0 + lfind(vlp, i);
     if (threadIdx.x == 0 && s_ovf) {
       const unsigned long long j = atomicAdd(&c.st->counters[3], 1ull);
@@ -797,29 +916,38 @@ __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const
   }
 }
 
-// Phase B, one segment: Atomic-Hook on pi of worklist pairs [p0, p1) (K per thread, each j a
-// coalesced read) and, when `overflowed` is set, of every arc of the windows listed as
-// overflowed (one CTA per window).
-template <typename OffT, bool SYM>
-__device__ __forceinline__ void tiled_phase_b(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
-                                              int V, OffT nnz, unsigned long long p0, unsigned long long p1,
-                                              bool overflowed, unsigned long long n_ovf, long long tid,
-                                              long long nthreads, const Ctl& c) {
+// Atomic-Hook on pi of worklist pairs [p0, p1), K per thread and step (each j a coalesced read),
+// with the pairs that reach the same two roots in a warp hooked once. The loop is warp-uniform
+// (lanes past the end carry no pair), as the deduplication needs.
+__device__ __forceinline__ void hook_worklist(int* pi, const int2* __restrict__ wl, unsigned long long p0,
+                                              unsigned long long p1, long long tid, long long nthreads, int V,
+                                              const Ctl& c) {
   constexpr int K = kPairK;
   const unsigned long long T = (unsigned long long)nthreads;
-  for (unsigned long long base = p0 + (unsigned long long)tid; base < p1; base += T * K) {
+  const unsigned long long lane = (unsigned long long)(threadIdx.x & 31);
+  for (unsigned long long base = p0 + (unsigned long long)tid; base - lane < p1; base += T * K) {
     int u[K], v[K];
     bool live[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const unsigned long long i = base + (unsigned long long)j * T;
       live[j] = i < p1;
-      const int2 e = live[j] ? c.wl[i] : make_int2(0, 0);
+      const int2 e = live[j] ? wl[i] : make_int2(0, 0);
       u[j] = e.x;
       v[j] = e.y;
     }
-    atomic_hook_k<K>(pi, u, v, live, V, c);
+    atomic_hook_k<K, true>(pi, u, v, live, V, c);
   }
+}
+
+// Phase B, one segment: Atomic-Hook on pi of worklist pairs [p0, p1) and, when `overflowed` is
+// set, of every arc of the windows listed as overflowed (one CTA per window).
+template <typename OffT, bool SYM>
+__device__ __forceinline__ void tiled_phase_b(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                              int V, OffT nnz, unsigned long long p0, unsigned long long p1,
+                                              bool overflowed, unsigned long long n_ovf, long long tid,
+                                              long long nthreads, const Ctl& c) {
+  hook_worklist(pi, c.wl, p0, p1, tid, nthreads, V, c);
   if (!overflowed) return;
   const int W = c.tile_w;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -830,7 +958,7 @@ __device__ __forceinline__ void tiled_phase_b(const OffT* __restrict__ rp, const
     if (!(u0 >= 0 && u0 <= u1 && u1 <= nnz)) continue;
     const OffT t0 = u0 + split_point<OffT>(u1 - u0, nwarps, warp);
     const OffT t1 = u0 + split_point<OffT>(u1 - u0, nwarps, warp + 1);
-    if (t0 < t1) hook_csr_range<OffT, SYM, false, kHookK>(rp, col, pi, V, t0, t1, c, w0);
+    if (t0 < t1) hook_csr_range<OffT, SYM, kHookK>(rp, col, pi, V, t0, t1, c, w0);
   }
 }
 

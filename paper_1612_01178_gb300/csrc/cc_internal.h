@@ -33,15 +33,19 @@ struct LaunchShape {
   int block;
 };
 
-// Blocks of the persistent kernel that fit on one SM at `block` threads (0 if it cannot run),
-// including the dynamic shared memory of the hierarchical hook.
+// Blocks of the cooperative kernel of p (the plain persistent driver, or phase B of the
+// hierarchical hook when p.tile_w > 0) that fit on one SM at `block` threads (0 if it cannot run).
 int persistent_blocks_per_sm(const Problem& p, int block);
 int stage_blocks_per_sm(const Problem& p, int block);
-// Dynamic shared memory of a launch for problem p.
-size_t dynamic_smem_bytes(const Problem& p, int block);
+// Blocks of the phase-A kernel of the hierarchical hook per SM, with its window in shared memory.
+int phase_a_blocks_per_sm(const Problem& p, int block);
 
 // One cooperative launch running init + all segments (Hook, barrier, Multi-Jump, barrier).
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
+
+// Hierarchical hook (p.tile_w > 0): the phase-A launch (shape sa, windows from a work counter),
+// then the cooperative phase-B launch (shape sb: worklist segments, each with a Multi-Jump).
+cudaError_t launch_two_phase(const Problem& p, const Ctl& c, LaunchShape sa, LaunchShape sb, cudaStream_t stream);
 
 // Fig. 4 as printed: init, then per segment one Hook launch and one Multi-Jump launch.
 // Returns the number of launches issued in *launches.

@@ -1,7 +1,7 @@
 // Single-graph kernels: the persistent driver of Fig. 4 (one cooperative launch, grid
-// barriers between Hook and Multi-Jump phases) and the per-phase kernels of the printed
-// host loop, for CSR (int32 / int64 offsets, plain or symmetrised, plain or hierarchical
-// hook) and COO inputs.
+// barriers between Hook and Multi-Jump phases), the two launches of the hierarchical hook, and
+// the per-phase kernels of the printed host loop, for CSR (int32 / int64 offsets, plain or
+// symmetrised) and COO inputs.
 #include "cc_internal.h"
 
 namespace cc {
@@ -26,43 +26,16 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-// Adaptive Hook-Compress (Fig. 4) over the arcs of a CSR graph, in one launch.
-// Plain:  init pi; for i in 1..s: Atomic-Hook(E_i); barrier; Multi-Jump(V); barrier.
-//         Hook phase i takes its work from counter i % 2; thread 0 zeroes the other counter
-//         during the phase, and the barriers in between publish the reset before its next use.
-// TILED:  phase A (window-local hooks in shared memory, pi written, worklist E' built);
-//         barrier; then Fig. 4 over E': s' = 2|E'|/|V| segments, each Atomic-Hook on pi
-//         followed by Multi-Jump(V).
-template <typename OffT, bool SYM, bool TILED>
+// Adaptive Hook-Compress (Fig. 4) over the arcs of a CSR graph, in one launch: init pi; for i
+// in 1..s: Atomic-Hook(E_i); barrier; Multi-Jump(V); barrier. Hook phase i takes its work from
+// counter i % 2; thread 0 zeroes the other counter during the phase, and the barriers in
+// between publish the reset before its next use.
+template <typename OffT, bool SYM>
 __device__ __forceinline__ void csr_persistent_body(const OffT* __restrict__ rp, const int* __restrict__ col,
-                                                    int* pi, int V, OffT nnz, int s, int* lp, const Ctl& c) {
+                                                    int* pi, int V, OffT nnz, int s, const Ctl& c) {
   if (ld_relaxed(&c.st->error) != 0) return;  // a pending error stops all device work
   unsigned epoch = 0;
   const long long tid = global_tid(), nt = global_threads();
-  if (TILED) {
-    tiled_phase_a<OffT, SYM>(rp, col, pi, V, nnz, lp, c);
-    if (!grid_sync(c, epoch)) return;
-    const unsigned long long cur = ld_volatile_u64(&c.st->counters[2]);
-    const unsigned long long n_pairs = cur < c.wl_cap ? cur : c.wl_cap;
-    unsigned long long n_ovf = ld_volatile_u64(&c.st->counters[3]);
-    n_ovf = n_ovf < (unsigned long long)c.ovf_cap ? n_ovf : (unsigned long long)c.ovf_cap;
-    if (n_pairs == 0 && n_ovf == 0) return;  // every tree is already a star rooted at its minimum
-    long long s2 = c.segments_b;
-    if (s2 <= 0) s2 = (long long)((2.0 * (double)n_pairs) / (double)V + 0.5);
-    s2 = s2 < 1 ? 1 : (s2 > 4096 ? 4096 : s2);
-    if (tid == 0) {
-      c.st->report[0] = n_pairs;
-      c.st->report[1] = (unsigned long long)s2;
-    }
-    for (long long i = 0; i < s2; ++i) {
-      tiled_phase_b<OffT, SYM>(rp, col, pi, V, nnz, split_point<unsigned long long>(n_pairs, s2, i),
-                               split_point<unsigned long long>(n_pairs, s2, i + 1), i == 0, n_ovf, tid, nt, c);
-      if (!grid_sync(c, epoch)) return;
-      multi_jump(pi, V, tid, nt, c);
-      if (i + 1 < s2 && !grid_sync(c, epoch)) return;
-    }
-    return;
-  }
   init_pi(pi, V, tid, nt);
   if (!grid_sync(c, epoch)) return;
   for (int i = 0; i < s; ++i) {
@@ -76,13 +49,57 @@ __device__ __forceinline__ void csr_persistent_body(const OffT* __restrict__ rp,
   }
 }
 
-template <typename OffT, bool SYM, bool TILED>
-__global__ void __launch_bounds__(kMaxBlock, TILED ? 1 : 2) k_csr_persistent(const OffT* __restrict__ rp,
-                                                              const int* __restrict__ col, int* pi, int V, OffT nnz,
-                                                              int s, Ctl c) {
-  extern __shared__ int dyn_smem[];
+template <typename OffT, bool SYM>
+__global__ void __launch_bounds__(kMaxBlock, 2) k_csr_persistent(const OffT* __restrict__ rp,
+                                                                 const int* __restrict__ col, int* pi, int V,
+                                                                 OffT nnz, int s, Ctl c) {
   phase_start(c);
-  csr_persistent_body<OffT, SYM, TILED>(rp, col, pi, V, nnz, s, dyn_smem, c);
+  csr_persistent_body<OffT, SYM>(rp, col, pi, V, nnz, s, c);
+  phase_end(c);
+}
+
+// Two-phase hierarchical hook, first launch: phase A (window-local hooks in shared memory, pi
+// written, worklist E' built). Windows are taken from a work counter, so the grid needs no
+// co-residency; at the default window two 1024-thread CTAs share an SM.
+template <typename OffT, bool SYM>
+__global__ void __launch_bounds__(kMaxBlock, 2) k_phase_a(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                          int* pi, int V, OffT nnz, Ctl c) {
+  extern __shared__ __align__(16) unsigned char dyn_smem_a[];
+  phase_start(c);
+  if (ld_relaxed(&c.st->error) == 0) tiled_phase_a<OffT, SYM, int>(rp, col, pi, V, nnz, dyn_smem_a, c);
+  if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + 1, now_ns());
+}
+
+// Second launch (cooperative): Fig. 4 over E', s' = 2|E'|/|V| segments, each Atomic-Hook on pi
+// followed by Multi-Jump(V). The windows whose worklist appends overflowed are hooked arc by
+// arc in the first segment.
+template <typename OffT, bool SYM>
+__global__ void __launch_bounds__(kMaxBlock, 1) k_phase_b(const OffT* __restrict__ rp, const int* __restrict__ col,
+                                                          int* pi, int V, OffT nnz, Ctl c) {
+  if (ld_relaxed(&c.st->error) == 0) {
+    unsigned epoch = 0;
+    const long long tid = global_tid(), nt = global_threads();
+    const unsigned long long cur = ld_volatile_u64(&c.st->counters[2]);
+    const unsigned long long n_pairs = cur < c.wl_cap ? cur : c.wl_cap;
+    unsigned long long n_ovf = ld_volatile_u64(&c.st->counters[3]);
+    n_ovf = n_ovf < (unsigned long long)c.ovf_cap ? n_ovf : (unsigned long long)c.ovf_cap;
+    if (n_pairs != 0 || n_ovf != 0) {  // else every tree is already a star rooted at its minimum
+      long long s2 = c.segments_b;
+      if (s2 <= 0) s2 = (long long)((2.0 * (double)n_pairs) / (double)V + 0.5);
+      s2 = s2 < 1 ? 1 : (s2 > 4096 ? 4096 : s2);
+      if (tid == 0) {
+        c.st->report[0] = n_pairs;
+        c.st->report[1] = (unsigned long long)s2;
+      }
+      for (long long i = 0; i < s2; ++i) {
+        tiled_phase_b<OffT, SYM>(rp, col, pi, V, nnz, split_point<unsigned long long>(n_pairs, s2, i),
+                                 split_point<unsigned long long>(n_pairs, s2, i + 1), i == 0, n_ovf, tid, nt, c);
+        if (!grid_sync(c, epoch)) break;
+        multi_jump(pi, V, tid, nt, c);
+        if (i + 1 < s2 && !grid_sync(c, epoch)) break;
+      }
+    }
+  }
   phase_end(c);
 }
 
@@ -236,12 +253,23 @@ cudaError_t launch_kernel(void (*kernel)(Args...), LaunchShape s, size_t smem, b
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// Calls f(kernel) with the persistent CSR kernel variant (symmetric / hierarchical) of p.
+// Calls f(kernel) with the cooperative CSR kernel of p: the plain persistent driver, or phase B
+// of the hierarchical hook.
 template <typename OffT, typename F>
 auto with_csr_persistent(const Problem& p, F&& f) {
   const bool tiled = p.tile_w > 0;
-  if (p.sym) return tiled ? f(k_csr_persistent<OffT, true, true>) : f(k_csr_persistent<OffT, true, false>);
-  return tiled ? f(k_csr_persistent<OffT, false, true>) : f(k_csr_persistent<OffT, false, false>);
+  if (p.sym) return tiled ? f(k_phase_b<OffT, true>) : f(k_csr_persistent<OffT, true>);
+  return tiled ? f(k_phase_b<OffT, false>) : f(k_csr_persistent<OffT, false>);
+}
+
+template <typename OffT, typename F>
+auto with_phase_a(const Problem& p, F&& f) {
+  return p.sym ? f(k_phase_a<OffT, true>) : f(k_phase_a<OffT, false>);
+}
+
+template <typename OffT, typename F>
+auto with_phase_b(const Problem& p, F&& f) {
+  return p.sym ? f(k_phase_b<OffT, true>) : f(k_phase_b<OffT, false>);
 }
 
 template <typename OffT, typename F>
@@ -251,15 +279,20 @@ auto with_csr_hook(const Problem& p, F&& f) {
 
 }  // namespace
 
-size_t dynamic_smem_bytes(const Problem& p, int block) {
-  return (p.kind == kKindCsr && p.tile_w > 0) ? tiled_smem_bytes(p.tile_w, block) : 0;
+size_t phase_a_smem_bytes(const Problem& p, int block) {
+  return tiled_smem_bytes(p.tile_w, block, (int)sizeof(int));
 }
 
 int persistent_blocks_per_sm(const Problem& p, int block) {
-  const size_t smem = dynamic_smem_bytes(p, block);
   if (p.kind == kKindCoo) return blocks_per_sm(k_coo_persistent, block, 0);
-  auto occ = [&](auto k) { return blocks_per_sm(k, block, smem); };
+  auto occ = [&](auto k) { return blocks_per_sm(k, block, 0); };
   return p.rp64 ? with_csr_persistent<long long>(p, occ) : with_csr_persistent<int>(p, occ);
+}
+
+int phase_a_blocks_per_sm(const Problem& p, int block) {
+  const size_t smem = phase_a_smem_bytes(p, block);
+  auto occ = [&](auto k) { return blocks_per_sm(k, block, smem); };
+  return p.rp64 ? with_phase_a<long long>(p, occ) : with_phase_a<int>(p, occ);
 }
 
 int stage_blocks_per_sm(const Problem& p, int block) {
@@ -271,16 +304,41 @@ int stage_blocks_per_sm(const Problem& p, int block) {
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
   if (p.kind == kKindCoo)
     return launch_kernel(k_coo_persistent, s, 0, true, stream, p.src, p.dst, p.pi, p.V, p.m, p.segments, c);
-  const size_t smem = dynamic_smem_bytes(p, s.block);
   if (p.rp64) {
     const long long* rp = static_cast<const long long*>(p.rp);
-    return with_csr_persistent<long long>(p, [&](auto k) {
-      return launch_kernel(k, s, smem, true, stream, rp, p.col, p.pi, p.V, (long long)p.m, p.segments, c);
+    return p.sym ? launch_kernel(k_csr_persistent<long long, true>, s, 0, true, stream, rp, p.col, p.pi, p.V,
+                                 (long long)p.m, p.segments, c)
+                 : launch_kernel(k_csr_persistent<long long, false>, s, 0, true, stream, rp, p.col, p.pi, p.V,
+                                 (long long)p.m, p.segments, c);
+  }
+  const int* rp = static_cast<const int*>(p.rp);
+  return p.sym ? launch_kernel(k_csr_persistent<int, true>, s, 0, true, stream, rp, p.col, p.pi, p.V, (int)p.m,
+                               p.segments, c)
+               : launch_kernel(k_csr_persistent<int, false>, s, 0, true, stream, rp, p.col, p.pi, p.V, (int)p.m,
+                               p.segments, c);
+}
+
+cudaError_t launch_two_phase(const Problem& p, const Ctl& c, LaunchShape sa, LaunchShape sb, cudaStream_t stream) {
+  const size_t smem = phase_a_smem_bytes(p, sa.block);
+  Ctl cb = c;
+  cb.phase_off = 1;  // slot 1 holds the end of phase A
+  if (p.rp64) {
+    const long long* rp = static_cast<const long long*>(p.rp);
+    cudaError_t e = with_phase_a<long long>(p, [&](auto k) {
+      return launch_kernel(k, sa, smem, false, stream, rp, p.col, p.pi, p.V, (long long)p.m, c);
+    });
+    if (e != cudaSuccess) return e;
+    return with_phase_b<long long>(p, [&](auto k) {
+      return launch_kernel(k, sb, 0, true, stream, rp, p.col, p.pi, p.V, (long long)p.m, cb);
     });
   }
   const int* rp = static_cast<const int*>(p.rp);
-  return with_csr_persistent<int>(p, [&](auto k) {
-    return launch_kernel(k, s, smem, true, stream, rp, p.col, p.pi, p.V, (int)p.m, p.segments, c);
+  cudaError_t e = with_phase_a<int>(p, [&](auto k) {
+    return launch_kernel(k, sa, smem, false, stream, rp, p.col, p.pi, p.V, (int)p.m, c);
+  });
+  if (e != cudaSuccess) return e;
+  return with_phase_b<int>(p, [&](auto k) {
+    return launch_kernel(k, sb, 0, true, stream, rp, p.col, p.pi, p.V, (int)p.m, cb);
   });
 }
 

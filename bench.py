@@ -818,8 +818,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(name), "peak_source": peak_kind,
                      "bytes_alg_per_launch": b_alg,
-                     "kernel": "k_csr_persistent<%s,SYM,%s>" % ("int" if g.row_ptr.dtype == np.int32 else "int64",
-                                                                 "two-phase" if info["tile_vertices"] else "plain"),
+                     "kernel": (("k_phase_a<%s,SYM> + k_phase_b<%s,SYM> (one labelling, both launches)"
+                                 if info["tile_vertices"] else "k_csr_persistent<%s,SYM>")
+                                % ((("int" if g.row_ptr.dtype == np.int32 else "int64"),) *
+                                   (2 if info["tile_vertices"] else 1))),
                      "kernel_ms_mean": ms, "kernel_ms_min": min(step_ms)},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -102,9 +102,10 @@ typedef struct cc_options {
                           co-resident is halved until it can. */
   int32_t grid_blocks; /* blocks per launch; 0 = all co-resident blocks (occupancy x SMs) */
   int32_t flags;       /* CC_FLAG_* */
-  int32_t chunk_arcs;  /* global Atomic-Hook work split: -1 or 0 = one fixed slice of the segment per
+  int32_t chunk_arcs;  /* global Atomic-Hook work split: -1 = one fixed slice of the segment per
                           warp; > 0 (a multiple of 32) = warps take chunks of this many arcs from a
-                          shared counter */
+                          shared counter; 0 = automatic (chunks of 2048 arcs when a segment holds
+                          at least 2048 arcs per warp of the launch, else fixed slices) */
   int32_t tile_vertices; /* window of the two-phase hierarchical Atomic-Hook (CSR, persistent mode):
                           a power of two, 256 .. 32768. Phase A hooks every arc whose two ends lie
                           in the same window of this many consecutive IDs in shared memory and

@@ -49,12 +49,20 @@ struct cc_ctx {
 namespace {
 
 constexpr long long kDefaultTimeoutNs = 2000000000LL;
-constexpr int kDefaultChunkArcs = -1;
+constexpr int kDefaultChunkArcs = 0;  // automatic
+// Automatic work split of the plain hook: warps take chunks of kAutoChunkArcs arcs from a counter
+// when a segment holds at least that many arcs per warp (a fixed slice per warp leaves the
+// grid waiting on the slowest slice of a skewed graph); smaller segments use fixed slices.
+constexpr int kAutoChunkArcs = 2048;
 // Default window of the two-phase hook: single graphs use 16384 vertices (64 KB of 32-bit local
 // parents, two 1024-thread CTAs per SM); the batched kernel keeps whole graphs of up to 32768
 // vertices in one CTA.
 constexpr int kDefaultTileVertices = 16384;
 constexpr int kBatchedTileVertices = 32768;
+// Widest automatic window of a single graph: 18432 x 4 bytes of local parents plus the per-warp
+// scratch of 32 warps still lets two 1024-thread CTAs share an SM's 228 KB.
+constexpr int kMaxAutoWindow = 18432;
+constexpr int kMinAutoWindow = 2048;
 constexpr int kMaxTileVertices = 32768;
 constexpr int kPlainBlock = 256;   // default block of the plain hook
 constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
@@ -84,7 +92,6 @@ cc_status cuda_fail(cc_ctx* ctx, cudaError_t e, const char* where) {
 
 void resolve_options(cc_options* o) {
   if (o->timeout_ns <= 0) o->timeout_ns = kDefaultTimeoutNs;
-  if (o->chunk_arcs == 0) o->chunk_arcs = kDefaultChunkArcs;
 }
 
 // Window of the two-phase hook for `want` vertices: a power of two, at least 256, no wider
@@ -93,6 +100,20 @@ int window_for(long long V, int want) {
   int w = 256;
   while (w < want && w < V) w <<= 1;
   return w;
+}
+
+// Automatic window (tile_vertices = 0, two-phase hook chosen): phase A hands windows to the
+// co-resident CTAs from a counter, so its time is set by the number of rounds of windows per
+// CTA. The window is the smallest multiple of 256 that covers V in whole rounds of all CTAs,
+// with no more rounds than kMaxAutoWindow needs (a window count just above a multiple of the
+// CTA count would leave most CTAs idle in the last round).
+int balanced_window(const cc_ctx* ctx, cc::Problem p, int block) {
+  p.tile_w = kMaxAutoWindow;
+  const long long ctas = (long long)std::max(1, cc::phase_a_blocks_per_sm(p, block)) * ctx->num_sms;
+  const long long rounds = std::max<long long>(1, (p.V + ctas * kMaxAutoWindow - 1) / (ctas * kMaxAutoWindow));
+  long long w = (p.V + rounds * ctas - 1) / (rounds * ctas);
+  w = (w + 255) / 256 * 256;
+  return (int)std::min<long long>(kMaxAutoWindow, std::max<long long>(kMinAutoWindow, w));
 }
 
 // Automatic hook choice (tile_vertices = 0): the two-phase hook pays off when most arcs join
@@ -296,6 +317,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     } else if (o.tile_vertices == 0) {
       const cc_status st = auto_window(ctx, p, &w);
       if (st != CC_OK) return st;
+      if (w > 0) w = balanced_window(ctx, p, o.block > 0 ? o.block : kTiledBlock);
     }
   }
   if (w > 0) {
@@ -332,6 +354,11 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     const long long cap = (long long)per_sm * ctx->num_sms;
     long long grid = o.grid_blocks > 0 ? std::min<long long>(o.grid_blocks, cap) : std::min(want, cap);
     cc::LaunchShape s{(int)grid, block};
+    if (o.chunk_arcs == 0) {
+      const long long warps = grid * (block / 32);
+      const long long per_segment = p.m / std::max(1, p.segments);
+      c.chunk_arcs = per_segment >= (long long)kAutoChunkArcs * warps ? kAutoChunkArcs : -1;
+    }
     c.skip_arrival_block = ctx->skip_arrival_block;
     ctx->skip_arrival_block = -1;
     cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);

@@ -42,6 +42,7 @@ enum ErrorSite : int {
   kSiteJumpGuard = 4,
   kSiteValidate = 5,
   kSiteFindGuard = 6,
+  kSiteWindowRow = 7,  // phase A: info = graph-local vertex whose row holds an endpoint outside [0, V)
 };
 
 // Status codes mirrored from cc.h (device code does not include the C header).
@@ -518,16 +519,18 @@ constexpr int kSinkPairs = 128;
 constexpr int kDeferCap = 64;
 constexpr int kWarpScratchBytes = kSinkPairs * (int)sizeof(int2) + kDeferCap * (int)sizeof(unsigned);
 
-// Flags a warp gathers during phase A (reported to the CTA at the end of the window).
-constexpr int kSinkOverflow = 1;  // a worklist append did not fit
-constexpr int kSinkBadArc = 2;    // an arc endpoint was outside [0, V)
+// Flags a lane gathers during phase A (reported at the end of the window): bit 0 = a worklist
+// append did not fit; bit 1 = an arc endpoint was outside [0, V), with (local row + 1) << 2 of
+// the last such row above them.
+constexpr int kSinkOverflow = 1;
+constexpr int kSinkBadArc = 2;
 
 struct WarpSink {
   int2* buf;   // kSinkPairs entries in shared memory, private to the warp, then kDeferCap
                // deferred local hooks
   int count;   // warp-uniform
   int dcount;  // warp-uniform, < 32 between calls
-  int flags;   // kSinkOverflow | kSinkBadArc, per lane
+  int flags;   // kSinkOverflow | kSinkBadArc | bad row, per lane
   __device__ __forceinline__ unsigned* dq() const { return reinterpret_cast<unsigned*>(buf + kSinkPairs); }
 };
 
@@ -563,18 +566,13 @@ template <typename LT>
 __device__ __forceinline__ bool local_hook_try(LT* lp, int a, int b) {
   const int pa = reinterpret_cast<volatile LT*>(lp)[a];
   const int pb = reinterpret_cast<volatile LT*>(lp)[b];
-  if (pa == pb) return true;
-  int H, L;
-  if (pb == b && b > pa) {
-    H = b;
-    L = pa;
-  } else if (pa == a && a > pb) {
-    H = a;
-    L = pb;
-  } else {
-    return false;
-  }
-  return cas_local(lp + H, H, L) == H;
+  const bool link_b = pb == b && b > pa;
+  const bool link_a = pa == a && a > pb;
+  const int H = link_b ? b : a;
+  const int L = link_b ? pa : pb;
+  bool done = pa == pb;
+  if (!done && (link_a || link_b)) done = cas_local(lp + H, H, L) == H;
+  return done;
 }
 
 // Queues the hooks that local_hook_try left (lanes with `take`) and finishes 32 of them, one per
@@ -783,22 +781,20 @@ template <typename OffT>
 __device__ __forceinline__ void load_group(const int* __restrict__ col, OffT x0, OffT x1, int g, int (&v)[kGroup]) {
 #pragma unroll
   for (int j = 0; j < kGroup; ++j) {
-    const OffT a = x0 + (OffT)(g * kGroup + j);
-    v[j] = a < x1 ? ld_stream(col + a) : 0;
+    const long long a = (long long)x0 + g * kGroup + j;  // no wrap for an int32 x1 near 2^31
+    v[j] = a < (long long)x1 ? ld_stream(col + a) : 0;
   }
 }
 
 // Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window. IDs
 // are local to the graph (< V); worklist entries get vbase added (the graph's first vertex in a
-// batch). `bad` records an endpoint outside [0, V).
+// batch). An endpoint outside [0, V) is only flagged here (no branch on the hot path);
+// phase_a_window reports it once per window.
 template <bool SYM, typename LT>
-__device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, long long a, int V, int w0, int nrows,
-                                            LT* lp, WarpSink& sink, int vbase, const Ctl& c) {
+__device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, int V, int w0, int nrows, LT* lp,
+                                            WarpSink& sink, int vbase, const Ctl& c) {
   const bool in_range = has && (unsigned)v < (unsigned)V;
-  if (has && !in_range) {
-    raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
-    sink.flags |= kSinkBadArc;
-  }
+  sink.flags = (has && !in_range) ? ((sink.flags & kSinkOverflow) | kSinkBadArc | ((i + 1) << 2)) : sink.flags;
   const bool live = in_range && (SYM ? (v > u) : (v != u));
   const int b = v - w0;
   const bool local = live && (unsigned)b < (unsigned)nrows;
@@ -838,27 +834,27 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
       const bool heavy = deg > kHeavyRow;
 #pragma unroll
       for (int j = 0; j < kGroup; ++j)
-        phase_a_arc<SYM, LT>(!heavy && j < deg, i, u, v[j], (long long)(a0 + j), V, w0, nrows, lp, sink, vbase, c);
+        phase_a_arc<SYM, LT>(!heavy && j < deg, i, u, v[j], V, w0, nrows, lp, sink, vbase, c);
       const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
       for (int g = 1; g * kGroup < maxdeg; ++g) {
         int w[kGroup];
         load_group<OffT>(col, a0, heavy ? a0 : a1, g, w);
 #pragma unroll
         for (int j = 0; j < kGroup; ++j)
-          phase_a_arc<SYM, LT>(!heavy && g * kGroup + j < deg, i, u, w[j], (long long)(a0 + g * kGroup + j), V, w0, nrows,
-                           lp, sink, vbase, c);
+          phase_a_arc<SYM, LT>(!heavy && g * kGroup + j < deg, i, u, w[j], V, w0, nrows, lp, sink, vbase, c);
       }
       unsigned hv = __ballot_sync(kFull, heavy);
       while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
         const int h = __ffs(hv) - 1;
         hv &= hv - 1;
         const int hi = __shfl_sync(kFull, i, h);
-        const OffT h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
-        for (OffT bb = h0; bb < h1; bb += 32) {
-          const OffT a = bb + lane;
+        // 64-bit positions: an int32 nnz near 2^31 must not wrap past the row's end
+        const long long h0 = (long long)__shfl_sync(kFull, a0, h), h1 = (long long)__shfl_sync(kFull, a1, h);
+        for (long long bb = h0; bb < h1; bb += 32) {
+          const long long a = bb + lane;
           const bool has = a < h1;
           const int vv = has ? ld_stream(col + a) : 0;
-          phase_a_arc<SYM, LT>(has, hi, w0 + hi, vv, (long long)a, V, w0, nrows, lp, sink, vbase, c);
+          phase_a_arc<SYM, LT>(has, hi, w0 + hi, vv, V, w0, nrows, lp, sink, vbase, c);
         }
       }
     }
@@ -866,9 +862,48 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
   defer_drain(sink, lp);
   sink_flush(sink, c);
   if (sink.flags & kSinkOverflow) *ovf = 1;
-  if (sink.flags & kSinkBadArc) *bad = 1;
+  if (sink.flags & kSinkBadArc) {
+    raise_error(c.st, kErrOutOfRange, kSiteWindowRow, (long long)w0 + (sink.flags >> 2) - 1);
+    *bad = 1;
+  }
   sink.flags = 0;
   __syncthreads();
+}
+
+// lp[i] = i for the window's rows, four entries per 16-byte shared store (lp is 16-byte aligned).
+template <typename LT>
+__device__ __forceinline__ void local_init(LT* lp, int nrows) {
+  if (sizeof(LT) == 4) {
+    int4* lp4 = reinterpret_cast<int4*>(lp);
+    for (int q = threadIdx.x; q < (nrows >> 2); q += blockDim.x) lp4[q] = make_int4(4 * q, 4 * q + 1, 4 * q + 2, 4 * q + 3);
+    for (int i = (nrows & ~3) + threadIdx.x; i < nrows; i += blockDim.x) lp[i] = (LT)i;
+  } else {
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = (LT)i;
+  }
+}
+
+// pi(w0 + i) = w0 + local root of i for the window's rows. Four consecutive rows per thread:
+// their parents, grandparents and great-grandparents are read level by level, a root found at
+// the second level ends the walk (deeper trees finish with lfind), and the four labels leave in
+// one 16-byte store when pi + w0 is 16-byte aligned.
+template <typename LT>
+__device__ __forceinline__ void publish_window(int* pi, int w0, LT* lp, int nrows) {
+  volatile LT* vlp = lp;
+  int q_end = 0;
+  if (sizeof(LT) == 4 && (reinterpret_cast<uintptr_t>(pi + w0) & 15) == 0) {
+    q_end = nrows >> 2;
+    for (int q = threadIdx.x; q < q_end; q += blockDim.x) {
+      int r[4], g[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = vlp[4 * q + k];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) g[k] = vlp[r[k]];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = g[k] == r[k] ? r[k] : lfind(vlp, g[k]);
+      *reinterpret_cast<int4*>(pi + w0 + 4 * q) = make_int4(w0 + r[0], w0 + r[1], w0 + r[2], w0 + r[3]);
+    }
+  }
+  for (int i = 4 * q_end + threadIdx.x; i < nrows; i += blockDim.x) pi[w0 + i] = w0 + lfind(vlp, i);
 }
 
 // Two-phase hierarchical Atomic-Hook, phase A. The vertices are cut into windows of W
@@ -903,11 +938,10 @@ __device__ __forceinline__ void tiled_phase_a(const OffT* __restrict__ rp, const
     if (k >= (unsigned long long)n_units) break;
     const int w0 = (int)(k * (unsigned long long)W);
     const int nrows = (V - w0) < W ? (V - w0) : W;
-    for (int i = threadIdx.x; i < nrows; i += blockDim.x) lp[i] = (LT)i;
+    local_init(lp, nrows);
     __syncthreads();
     phase_a_window<OffT, SYM, LT>(rp, col, V, nnz, w0, nrows, 0, lp, sink, &s_ovf, &s_bad, c);
-    volatile LT* vlp = lp;
-    for (int i = threadIdx.x; i < nrows; i += blockDim.x) pi[w0 + i] = w0 + lfind(vlp, i);
+    publish_window(pi, w0, lp, nrows);
     if (threadIdx.x == 0 && s_ovf) {
       const unsigned long long j = atomicAdd(&c.st->counters[3], 1ull);
       if (j < (unsigned long long)c.ovf_cap) c.ovf_units[j] = (int)k;

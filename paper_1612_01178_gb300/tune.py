@@ -22,7 +22,7 @@ SEARCH = [
     ("tile_vertices", [0, -1, 8192, 16384, 32768]),
     ("segments", [0, 1, 2, 4, 8, -1]),
     ("block", [0, 256, 512, 1024]),
-    ("chunk_arcs", [-1, 1024]),
+    ("chunk_arcs", [0, -1, 1024, 2048]),
 ]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gb300_cc_tune.json")
@@ -69,7 +69,7 @@ class Tuner:
         log = [(dict(best), best_ms)]
         for name, values in space:
             for v in values:
-                if best.get(name, 0 if name != "chunk_arcs" else -1) == v:
+                if best.get(name, 0) == v:
                     continue
                 cand = dict(best)
                 cand[name] = v

@@ -57,7 +57,7 @@ def test_status_strings_and_defaults(lib):
     for code in range(7):
         assert lib.cc_status_string(code)
     o = cc.default_options()
-    assert o.block == 0 and o.tile_vertices == 0 and o.chunk_arcs == -1
+    assert o.block == 0 and o.tile_vertices == 0 and o.chunk_arcs == 0
     assert o.timeout_ns == 2_000_000_000 and o.mode == cc.CC_MODE_AUTO
 
 

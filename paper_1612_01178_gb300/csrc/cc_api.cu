@@ -66,6 +66,7 @@ constexpr int kMinAutoWindow = 2048;
 constexpr int kMaxTileVertices = 32768;
 constexpr int kPlainBlock = 256;   // default block of the plain hook
 constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
+constexpr int kPhaseABlock = 1024; // default block of its phase-A launch
 constexpr int kSampleThreads = 16384;
 constexpr double kLocalFractionForTiles = 0.5;
 constexpr int kPhaseSlots = 64;
@@ -317,7 +318,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     } else if (o.tile_vertices == 0) {
       const cc_status st = auto_window(ctx, p, &w);
       if (st != CC_OK) return st;
-      if (w > 0) w = balanced_window(ctx, p, o.block > 0 ? o.block : kTiledBlock);
+      if (w > 0) w = balanced_window(ctx, p, o.block > 0 ? o.block : kPhaseABlock);
     }
   }
   if (w > 0) {
@@ -377,7 +378,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     }
     if (e == cudaSuccess && p.tile_w > 0) {
       // Phase A: one CTA per window at most, as many as are co-resident.
-      int block_a = o.block > 0 ? o.block : kTiledBlock;
+      int block_a = o.block > 0 ? o.block : kPhaseABlock;
       int per_sm_a = cc::phase_a_blocks_per_sm(p, block_a);
       while (per_sm_a <= 0 && block_a > 32) {
         block_a /= 2;

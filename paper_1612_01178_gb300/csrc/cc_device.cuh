@@ -234,17 +234,30 @@ __device__ __forceinline__ int root_from2(int* pi, int a, int pa, int ga) {
 // are loaded together and all first CASes are issued together, so a thread keeps up to 2K
 // loads or K atomics in flight instead of one dependent chain; deeper walks and failed CASes
 // then finish one edge at a time exactly as in atomic_hook.
-// DEDUP (the whole warp must call, converged): lanes whose edge j found the same pair of roots
-// (H, L) leave it to the lowest such lane, whose hook joins exactly those two trees; this keeps
-// thousands of CASes off one root when many edges join the same two components.
+// DEDUP (the whole warp must call, converged): lanes whose edge j has the same pair of parents
+// (pi(u), pi(v)), or later the same pair of roots (H, L), leave it to the lowest such lane, whose
+// hook joins exactly those two trees (u and v lie in them); this keeps thousands of root walks
+// and CASes off the same few roots when many edges join the same two components.
 template <int K, bool DEDUP = false>
-__device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const int (&v)[K], const bool (&live)[K],
+__device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const int (&v)[K], const bool (&live_in)[K],
                                               int V, const Ctl& c) {
   int pu[K], pv[K];
+  bool live[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
+    live[j] = live_in[j];
     pu[j] = live[j] ? ld_pi(pi + u[j]) : 0;
     pv[j] = live[j] ? ld_pi(pi + v[j]) : 0;
+  }
+  if (DEDUP) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const unsigned long long key =
+          live[j] ? (((unsigned long long)(unsigned)pu[j] << 32) | (unsigned)pv[j]) : ~0ull;
+      const unsigned grp = __match_any_sync(kFull, key);
+      live[j] = live[j] && lane == __ffs(grp) - 1;
+    }
   }
   int gu[K], gv[K];
 #pragma unroll

@@ -30,6 +30,8 @@ struct cc_ctx {
   size_t d_ovf_n = 0;
   long long* d_unit_start = nullptr;  // batched: first window of each graph
   size_t d_unit_start_n = 0;
+  long long* d_chunk_start = nullptr;  // batched: chunk table of the windows hooked arc by arc
+  size_t d_chunk_start_n = 0;
   // automatic hook choice: locality sample buffer and the last decision
   unsigned long long* d_sample = nullptr;
   unsigned long long* h_sample = nullptr;
@@ -585,7 +587,8 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
                                                                         std::max<long long>(total_vertices, 1 << 20)));
   if (grow_buffer(&ctx->d_unit_start, &ctx->d_unit_start_n, (size_t)n_graphs + 1) != cudaSuccess ||
       grow_buffer(&ctx->d_wl, &ctx->d_wl_pairs, cap) != cudaSuccess ||
-      grow_buffer(&ctx->d_ovf, &ctx->d_ovf_n, n_windows) != cudaSuccess) {
+      grow_buffer(&ctx->d_ovf, &ctx->d_ovf_n, n_windows) != cudaSuccess ||
+      grow_buffer(&ctx->d_chunk_start, &ctx->d_chunk_start_n, n_windows + 2) != cudaSuccess) {
     std::snprintf(ctx->last_error, sizeof(ctx->last_error), "batched scratch allocation failed");
     return CC_ERR_OOM;
   }
@@ -601,7 +604,8 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   ctx->skip_arrival_block = -1;
   p.unit_start = ctx->d_unit_start;
   p.plain_units = ctx->d_ovf;
-  p.plain_cap = (int)std::min<size_t>(ctx->d_ovf_n, INT32_MAX);
+  p.plain_cap = (int)std::min<size_t>(std::min(ctx->d_ovf_n, ctx->d_chunk_start_n - 2), INT32_MAX);
+  p.plain_chunk_start = ctx->d_chunk_start;
   p.sym = sym;
 
   cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
@@ -814,6 +818,7 @@ void cc_destroy(cc_ctx* ctx) {
     if (ctx->d_wl) cudaFree(ctx->d_wl);
     if (ctx->d_ovf) cudaFree(ctx->d_ovf);
     if (ctx->d_unit_start) cudaFree(ctx->d_unit_start);
+    if (ctx->d_chunk_start) cudaFree(ctx->d_chunk_start);
     if (ctx->d_sample) cudaFree(ctx->d_sample);
     if (ctx->h_sample) cudaFreeHost(ctx->h_sample);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -26,6 +26,12 @@ namespace cc {
 namespace {
 
 constexpr int kMaxBlockB = 1024;
+// Windows hooked arc by arc are cut into chunks, which warps take from a counter: a fixed split
+// leaves the grid waiting on the slowest piece of a skewed graph when a batch has few such
+// windows. A chunk is 2048 arcs, or less when the batch has fewer than four such chunks per warp
+// (down to 128 arcs), so that small batches still spread over every warp.
+constexpr int kPlainChunkArcs = 2048;
+constexpr int kMinPlainChunkArcs = 128;
 
 struct Batch {
   int n_graphs;
@@ -39,6 +45,8 @@ struct Batch {
   long long* unit_start;   // [n_graphs + 1] first window of each graph (filled by the kernel)
   int* plain_units;        // windows hooked arc by arc in phase B
   int plain_cap;
+  long long* plain_chunk_start;  // [plain_cap + 2] first chunk of each such window, then the chunk
+                                 // size (filled by the kernel)
   int total_v;             // label arena size (batch-global IDs are below it)
   long long row_elems;     // descriptor mode: row-offset arena size
   long long arc_elems;     // descriptor mode: arc arena size
@@ -142,8 +150,20 @@ __device__ __forceinline__ UnitInfo unit_info(const Batch& b, long long u, int W
   return ui;
 }
 
+// Graphs of one window are labelled by one CTA in shared memory, unless the batch has fewer
+// windows than CTAs and the graph has more than kOneCtaArcs arcs: the other CTAs would then idle
+// while one walks all its arcs, so such a graph is hooked arc by arc on pi in phase B instead
+// (with batch-global IDs, like a window without locality).
+constexpr long long kOneCtaArcs = 8192;
+__device__ __forceinline__ bool one_cta(const UnitInfo& ui, long long n_units) {
+  return ui.single && (n_units >= (long long)gridDim.x || ui.nnz <= kOneCtaArcs);
+}
+
 // Fraction test of one window's locality by warp 0: the middle arc of 32 rows spread over the
-// window; true when at least half of the sampled arcs stay in the window.
+// window; true when the fraction f of sampled arcs that stay in the window is at least halfway
+// from what random endpoints would give (nrows / V_g) to 1: f >= (1 + nrows / V_g) / 2. For
+// large graphs that is one half; a graph of two windows needs three quarters, since random
+// arcs already stay in a window half the time there.
 __device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
   const int lane = threadIdx.x & 31;
   const int r = ui.w0 + (int)(((long long)lane * ui.nrows) / 32);
@@ -158,7 +178,7 @@ __device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
   }
   const int ns = __popc(__ballot_sync(kFull, sampled));
   const int nl = __popc(__ballot_sync(kFull, local));
-  return 2 * nl >= ns;
+  return 2ll * nl * ui.vg >= (long long)ns * ((long long)ui.vg + ui.nrows);
 }
 
 template <bool SYM>
@@ -167,6 +187,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   __shared__ long long s_total;
   __shared__ unsigned long long s_unit;
   __shared__ int s_ovf, s_bad, s_plain;
+  __shared__ int s_warp_bad[kMaxBlockB / 32];
   if (ld_relaxed(&c.st->error) != 0) return;
   unsigned epoch = 0;
   const int W = c.tile_w;
@@ -204,8 +225,14 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     const UnitInfo ui = unit_info(b, (long long)k, W);
     for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) lp[i] = i;
     if (threadIdx.x < 32) {  // warp 0 decides how the window is hooked
+      // With fewer windows than CTAs, phase A would leave most of the GPU idle while a few
+      // CTAs walk whole windows: every window (but those of graphs small enough for one CTA)
+      // is then hooked arc by arc in phase B, spread over all warps.
       bool local = true;
-      if (!ui.single) local = c.window_mode == kWindowsPlain ? false : window_is_local(ui);
+      if (!ui.single)
+        local = (c.window_mode == kWindowsPlain || n_units < (long long)gridDim.x) ? false : window_is_local(ui);
+      else if (!one_cta(ui, n_units))
+        local = false;
       if (ui.nnz > 0x7fffffffLL) {  // graph too large for int32 row offsets: reported, not hooked
         local = true;
         if (threadIdx.x == 0) {
@@ -230,7 +257,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       else
         __syncthreads();
       volatile int* vlp = lp;
-      if (ui.single) {
+      if (one_cta(ui, n_units)) {
         for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[ui.vbase + i] = lfind(vlp, i);
       } else {
         const int base = ui.vbase + ui.w0;
@@ -257,34 +284,78 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     c.st->report[0] = n_pairs;
     c.st->report[1] = (unsigned long long)s2;
   }
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // Chunk table of the windows hooked arc by arc (block 0): window j owns chunks
+  // [chunk_start[j], chunk_start[j + 1]) of chunk_start[n_plain + 1] arcs each; a window whose
+  // row offsets are inconsistent gets one chunk, which reports it.
+  if (n_plain > 0) {
+    if (blockIdx.x == 0) {
+      long long arcs = 0;
+      for (unsigned long long j = threadIdx.x; j < n_plain; j += blockDim.x) {
+        const UnitInfo ui = unit_info(b, b.plain_units[j], W);
+        const int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
+        if (a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz) arcs += a1 - a0;
+      }
+      block_scan(arcs, s_warp_sums, &s_total);
+      const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+      long long chunk = s_total / (4 * warps);
+      chunk = chunk < kMinPlainChunkArcs ? kMinPlainChunkArcs : (chunk > kPlainChunkArcs ? kPlainChunkArcs : chunk);
+      chunk = (chunk + 31) & ~31ll;
+      long long carry = 0;
+      if (threadIdx.x == 0) {
+        b.plain_chunk_start[0] = 0;
+        b.plain_chunk_start[n_plain + 1] = chunk;
+      }
+      for (unsigned long long base = 0; base < n_plain; base += blockDim.x) {
+        const unsigned long long j = base + threadIdx.x;
+        long long n = 0;
+        if (j < n_plain) {
+          const UnitInfo ui = unit_info(b, b.plain_units[j], W);
+          const int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
+          n = (a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz) ? ((long long)(a1 - a0) + chunk - 1) / chunk : 1;
+        }
+        const long long incl = block_scan(n, s_warp_sums, &s_total);
+        if (j < n_plain) b.plain_chunk_start[j + 1] = carry + incl;
+        carry += s_total;
+      }
+    }
+    if (!grid_sync(c, epoch)) return;
+  }
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   for (long long seg = 0; seg < s2; ++seg) {
     const unsigned long long p0 = split_point<unsigned long long>(n_pairs, s2, seg);
     const unsigned long long p1 = split_point<unsigned long long>(n_pairs, s2, seg + 1);
     hook_worklist(b.labels, c.wl, p0, p1, tid, nt, b.total_v, c);
-    if (seg == 0) {  // windows without locality: every arc on pi, each window split over `parts` CTAs
-      const unsigned long long parts = split_factor(n_plain, gridDim.x);
-      for (unsigned long long item = blockIdx.x; item < n_plain * parts; item += gridDim.x) {
-        const UnitInfo ui = unit_info(b, b.plain_units[item / parts], W);
-        const long long part = (long long)(item % parts);
-        if (threadIdx.x == 0) s_bad = 0;
-        __syncthreads();
-        int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
+    if (seg == 0 && n_plain > 0) {  // windows without locality: every arc on pi, in chunks from a counter
+      const long long n_chunks = *reinterpret_cast<volatile long long*>(b.plain_chunk_start + n_plain);
+      const long long chunk = *reinterpret_cast<volatile long long*>(b.plain_chunk_start + n_plain + 1);
+      if (lane == 0) s_warp_bad[warp] = 0;
+      __syncwarp();
+      for (;;) {
+        long long t = 0;
+        if (lane == 0) t = (long long)atomicAdd(&c.st->counters[1], 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_chunks) break;
+        const int j = graph_of_unit(b.plain_chunk_start, (int)n_plain, t);
+        const UnitInfo ui = unit_info(b, b.plain_units[j], W);
+        const int a0 = ui.rp[ui.w0], a1 = ui.rp[ui.w0 + ui.nrows];
         if (a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz) {
-          const int p0 = a0 + split_point<int>(a1 - a0, (long long)parts, part);
-          const int p1 = a0 + split_point<int>(a1 - a0, (long long)parts, part + 1);
-          a0 = p0;
-          a1 = p1;
-          const int t0 = a0 + split_point<int>(a1 - a0, nwarps, warp);
-          const int t1 = a0 + split_point<int>(a1 - a0, nwarps, warp + 1);
+          const long long k = t - b.plain_chunk_start[j];
+          const int t0 = (int)((long long)a0 + k * chunk);
+          const int t1 = (long long)t0 + chunk < (long long)a1 ? (int)((long long)t0 + chunk) : a1;
           if (t0 < t1)
-            hook_csr_range<int, SYM, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, ui.vbase, &s_bad);
-        } else if (threadIdx.x == 0) {
+            hook_csr_range<int, SYM, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, ui.vbase,
+                                             s_warp_bad + warp);
+        } else if (lane == 0) {
           raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
-          s_bad = 1;
+          s_warp_bad[warp] = 1;
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && s_bad && b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+        __syncwarp();
+        if (lane == 0 && s_warp_bad[warp]) {
+          if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+          s_warp_bad[warp] = 0;
+        }
+        __syncwarp();
       }
     }
     if (!grid_sync(c, epoch)) return;
@@ -292,7 +363,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     const unsigned long long vparts = split_factor((unsigned long long)n_units, gridDim.x);
     for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * vparts; item += gridDim.x) {
       const UnitInfo ui = unit_info(b, (long long)(item / vparts), W);
-      if (ui.single) continue;
+      if (one_cta(ui, n_units)) continue;
       const long long part = (long long)(item % vparts);
       const int base = ui.vbase + ui.w0;
       const int i0 = split_point<int>(ui.nrows, (long long)vparts, part);
@@ -309,7 +380,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   const unsigned long long cparts = split_factor((unsigned long long)n_units, gridDim.x);
   for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * cparts; item += gridDim.x) {
     const UnitInfo ui = unit_info(b, (long long)(item / cparts), W);
-    if (ui.single) continue;
+    if (one_cta(ui, n_units)) continue;
     const long long part = (long long)(item % cparts);
     const int base = ui.vbase + ui.w0;
     const int i0 = split_point<int>(ui.nrows, (long long)cparts, part);
@@ -363,6 +434,7 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
   b.unit_start = p.unit_start;
   b.plain_units = p.plain_units;
   b.plain_cap = p.plain_cap;
+  b.plain_chunk_start = p.plain_chunk_start;
   b.total_v = (int)p.total_v;
   b.row_elems = p.row_elems;
   b.arc_elems = p.arc_elems;

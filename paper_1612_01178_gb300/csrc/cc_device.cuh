@@ -526,7 +526,7 @@ __device__ __forceinline__ int resolve_row(const OffT* __restrict__ rp, int V, i
 
 // Per-warp staging buffer in shared memory for the worklist of the two-phase hook: arcs are
 // appended by ballot (no atomics) and flushed to the global worklist with one atomic per flush.
-constexpr int kSinkPairs = 128;
+constexpr int kSinkPairs = 112;
 // Local hooks that the fast path of phase A could not finish wait in a per-warp queue of
 // kDeferCap packed pairs (two 16-bit local indices) and are finished 32 at a time.
 constexpr int kDeferCap = 64;
@@ -762,6 +762,19 @@ __host__ __device__ __forceinline__ size_t tiled_smem_bytes(int W, int block, in
 
 // Rows with more arcs than this are walked by a whole warp in phase A.
 constexpr int kHeavyRow = 32;
+// Rows of more than kHeavyRow arcs that a window can hand to the whole CTA (more are walked by
+// the warp that found them).
+constexpr int kHeavyCap = 128;
+
+// Rows of a window handed to the whole CTA: row i has arcs [a0, a1); blocks of 32 arcs are
+// numbered across the rows (prefix[h] = first block of row h).
+struct HeavyRows {
+  int n;
+  int row[kHeavyCap];
+  long long a0[kHeavyCap];
+  long long a1[kHeavyCap];
+  int prefix[kHeavyCap + 1];
+};
 // Arcs of a row loaded together in phase A.
 constexpr int kGroup = 4;
 
@@ -822,15 +835,21 @@ __device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, int V
 // forest. Warps take 32-row chunks (one row per lane) in an interleaved order, so the CTA sweeps
 // the window roughly in ID order and new vertices mostly join components that already have
 // short paths to their roots. Row offsets are loaded one chunk ahead. Rows of more than
-// kHeavyRow arcs are walked by the whole warp, 32 arcs at a time.
+// kHeavyRow arcs are set aside (up to kHeavyCap per window) and walked after the light rows by
+// all warps of the CTA together, 32 consecutive arcs per warp step, so one hub row does not
+// hold its warp, and with it the window, for thousands of steps; past kHeavyCap the warp that
+// found a heavy row walks it itself.
 template <typename OffT, bool SYM, typename LT>
 __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, const int* __restrict__ col, int V,
                                                OffT nnz, int w0, int nrows, int vbase, LT* lp, WarpSink& sink,
                                                volatile int* ovf, volatile int* bad, const Ctl& c) {
+  __shared__ HeavyRows s_heavy;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int step = nwarps * 32;
   const int r_begin = warp * 32;
   const int r_end = nrows;
+  if (threadIdx.x == 0) s_heavy.n = 0;
+  __syncthreads();
   if (r_begin < r_end) {  // warp-uniform
     OffT a0, a1, na0, na1;
     load_row_span<OffT>(rp, w0, r_begin + lane, r_end, na0, na1);
@@ -856,8 +875,18 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
         for (int j = 0; j < kGroup; ++j)
           phase_a_arc<SYM, LT>(!heavy && g * kGroup + j < deg, i, u, w[j], V, w0, nrows, lp, sink, vbase, c);
       }
-      unsigned hv = __ballot_sync(kFull, heavy);
-      while (hv) {  // heavy rows: the warp walks each one 32 arcs at a time
+      bool handed = false;
+      if (heavy) {
+        const int slot = atomicAdd(&s_heavy.n, 1);
+        if (slot < kHeavyCap) {
+          s_heavy.row[slot] = i;
+          s_heavy.a0[slot] = (long long)a0;
+          s_heavy.a1[slot] = (long long)a1;
+          handed = true;
+        }
+      }
+      unsigned hv = __ballot_sync(kFull, heavy && !handed);
+      while (hv) {  // heavy rows the CTA list could not take: the warp walks each one 32 arcs at a time
         const int h = __ffs(hv) - 1;
         hv &= hv - 1;
         const int hi = __shfl_sync(kFull, i, h);
@@ -870,6 +899,40 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
           phase_a_arc<SYM, LT>(has, hi, w0 + hi, vv, V, w0, nrows, lp, sink, vbase, c);
         }
       }
+    }
+  }
+  __syncthreads();
+  const int nh = s_heavy.n < kHeavyCap ? s_heavy.n : kHeavyCap;
+  if (nh > 0) {  // CTA-uniform: the handed-over heavy rows, 32-arc blocks spread over all warps
+    if (warp == 0) {
+      int carry = 0;
+      for (int h0 = 0; h0 < nh; h0 += 32) {
+        const int h = h0 + lane;
+        int nb = h < nh ? (int)((s_heavy.a1[h] - s_heavy.a0[h] + 31) >> 5) : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(kFull, nb, d);
+          if (lane >= d) nb += y;
+        }
+        if (h < nh) s_heavy.prefix[h + 1] = carry + nb;
+        carry += __shfl_sync(kFull, nb, 31);
+      }
+      if (lane == 0) s_heavy.prefix[0] = 0;
+    }
+    __syncthreads();
+    const int total = s_heavy.prefix[nh];
+    for (int k = warp; k < total; k += nwarps) {
+      int lo = 0, hi = nh;  // prefix[lo] <= k < prefix[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_heavy.prefix[mid] <= k) lo = mid;
+        else hi = mid;
+      }
+      const int hr = s_heavy.row[lo];
+      const long long a = s_heavy.a0[lo] + 32ll * (k - s_heavy.prefix[lo]) + lane;
+      const bool has = a < s_heavy.a1[lo];
+      const int vv = has ? ld_stream(col + a) : 0;
+      phase_a_arc<SYM, LT>(has, hr, w0 + hr, vv, V, w0, nrows, lp, sink, vbase, c);
     }
   }
   defer_drain(sink, lp);

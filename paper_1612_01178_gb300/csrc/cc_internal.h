@@ -75,6 +75,7 @@ struct BatchProblem {
   long long* unit_start;
   int* plain_units;
   int plain_cap;
+  long long* plain_chunk_start;  // [plain_cap + 2] chunk table of plain_units and chunk size (kernel-filled)
   long long total_v;    // label arena size
   long long row_elems;  // descriptor mode: arena sizes
   long long arc_elems;

@@ -11,11 +11,14 @@ the host. The loop:
      wait behind it, so a large request cannot starve). Its row offsets and arcs are copied in on
      the copy-in stream right away, while the device may still be busy with an earlier batch.
   3. When the compute stream is idle, every admitted request not yet launched goes into ONE
-     descriptor-mode batched launch (cc_labels_batched_desc) that waits on their copy-in events.
-     Requests arriving meanwhile are admitted and copied in during that launch: their copies
-     overlap the running batch, and they form the next one.
-  4. When a batch finishes, each request's labels are copied out on the copy-out stream; once a
-     copy lands, the request is complete and its arena slices are freed.
+     descriptor-mode batched launch (cc_labels_batched_desc) that waits on their copy-in events;
+     a batch of at most `single_max` requests is launched instead as back-to-back single-graph
+     launches, which cost less for few graphs. Requests arriving meanwhile are admitted and
+     copied in during that launch: their copies overlap the running batch, and they form the
+     next one.
+  4. With the launch, each request's label copy-out is queued on the copy-out stream behind the
+     batch's completion event; once a copy lands, the request is complete and its arena slices
+     are freed.
 
 Latency = completion time - arrival time (host clock). All device work is the library's CUDA
 kernels and CUDA copies; this module only schedules them.
@@ -136,10 +139,13 @@ class Server:
         self.s_out = torch.cuda.Stream(self.dev)
         self.s_cc = torch.cuda.Stream(self.dev)
         self.cc = ccapi.ConnectedComponents(device, stream=self.s_cc, flags=flags)
-        # a batch of one request goes through the single-graph entry point (lower fixed cost);
-        # the plain hook avoids the one-off locality sample, which would synchronise the loop
+        # a batch of at most `single_max` requests goes through the single-graph entry point, one
+        # launch per request back to back on the compute stream (lower fixed cost than one
+        # batched launch); the plain hook avoids the one-off locality sample, which would
+        # synchronise the loop
         self.cc_one = ccapi.ConnectedComponents(device, stream=self.s_cc, flags=flags, tile_vertices=-1)
         self.single_fast_path = True
+        self.single_max = 4
         self.pin_results = pin_results
         self.batches = []  # (n_requests, n_arcs) per launch, for reporting
 
@@ -196,19 +202,19 @@ class Server:
     def launch(self, batch, now: float):
         torch = self.torch
         n = len(batch)
-        if n == 1 and self.single_fast_path:
-            r = batch[0]
-            lo, ro, ao = r.slots
-            r.t_launch = now
-            self.s_cc.wait_event(r.ev_in)
-            V, E = r.n_vertices, r.n_arcs
-            ccapi.cc_labels_csr(self.cc_one.handle, self.rows[ro: ro + V + 1], self.arcs[ao: ao + E],
-                                self.labels[lo: lo + V])
+        if n <= self.single_max and self.single_fast_path:
+            for r in batch:
+                lo, ro, ao = r.slots
+                r.t_launch = now
+                self.s_cc.wait_event(r.ev_in)
+                V, E = r.n_vertices, r.n_arcs
+                ccapi.cc_labels_csr(self.cc_one.handle, self.rows[ro: ro + V + 1], self.arcs[ao: ao + E],
+                                    self.labels[lo: lo + V])
             with torch.cuda.stream(self.s_cc):
-                self.status_dev[:1].zero_()
+                self.status_dev[:n].zero_()
             ev = torch.cuda.Event()
             ev.record(self.s_cc)
-            self.batches.append((1, E))
+            self.batches.append((n, sum(r.n_arcs for r in batch)))
             return ev
         for i, r in enumerate(batch):
             lo, ro, ao = r.slots
@@ -272,12 +278,13 @@ class Server:
             while queue and self.try_admit(queue[0], now):
                 admitted.append(queue.pop(0))
             if running is not None and running[1].query():
-                self.copy_out(running[0], running[1])
                 finishing.extend(running[0])
                 running = None
             if running is None and admitted:
                 batch, admitted = admitted[:self.max_batch], admitted[self.max_batch:]
-                running = (batch, self.launch(batch, now))
+                ev = self.launch(batch, now)
+                self.copy_out(batch, ev)  # the copy-out stream waits for the batch on the device
+                running = (batch, ev)
             still = []
             for r in finishing:
                 if r.ev_out.query():

@@ -495,13 +495,20 @@ __device__ __forceinline__ int window_count(OffT e, OffT a) {
 // holds the end of row r + l, so the row is r + (number of window ends <= aq). When a lane's
 // arc lies past the window (rows with few or no arcs), the warp searches row_ptr from r + 32.
 // Returns V if no row exists (only when row_ptr[V] != n_arcs). Afterwards r is the row of the
-// arc of lane `last` (the batch's last valid lane), the start of the next window.
+// arc of lane `last` (the batch's last valid lane), the start of the next window. (rc, ec)
+// caches the end ec of row rc: while the batch's last arc lies before the end of row r, every
+// arc of the batch is in row r (arcs only increase), and the row needs no load and no search.
 template <typename OffT>
 __device__ __forceinline__ int resolve_row(const OffT* __restrict__ rp, int V, int& r, OffT aq, bool valid,
-                                           int last) {
+                                           int last, int& rc, OffT& ec) {
   const int lane = threadIdx.x & 31;
+  const OffT alast = __shfl_sync(kFull, aq, last);
+  if (rc == r && alast < ec) return r;  // warp-uniform
   const long long wi = (long long)r + 1 + lane;
   OffT e = ld_ro(rp + (wi < V ? wi : V));
+  rc = r;
+  ec = __shfl_sync(kFull, e, 0);
+  if (alast < ec) return r;
   int cnt = window_count<OffT>(e, aq);
   int u = cnt < 32 ? r + cnt : -1;
   unsigned pend = __ballot_sync(kFull, valid && u < 0);
@@ -649,6 +656,8 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
                                                volatile int* bad = nullptr) {
   const int lane = threadIdx.x & 31;
   int r = warp_row_search<OffT>(rp, lo_row, V, t0);
+  int rc = -1;  // row whose end ec is cached by resolve_row
+  OffT ec = 0;
   int vn[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -678,7 +687,7 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         const OffT a = bj + lane;
         const bool valid = a < t1;
         const long long rem = (long long)(t1 - bj) - 1;
-        u[j] = resolve_row<OffT>(rp, V, r, valid ? a : bj, valid, rem < 31 ? (int)rem : 31);
+        u[j] = resolve_row<OffT>(rp, V, r, valid ? a : bj, valid, rem < 31 ? (int)rem : 31, rc, ec);
         if (valid) {
           const bool in_range = (unsigned)v[j] < (unsigned)V && (unsigned)u[j] < (unsigned)V;
           if (!in_range) {

@@ -312,7 +312,6 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
 
   // Two-phase hierarchical hook (CSR, persistent mode): windows of W vertices.
   p.tile_w = 0;
-  p.unit_arcs = 0;
   int w = 0;
   if (p.kind == cc::kKindCsr && mode == CC_MODE_PERSISTENT && p.m > 0) {
     if (o.tile_vertices > 0) {

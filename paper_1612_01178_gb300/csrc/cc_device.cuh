@@ -55,7 +55,6 @@ struct Ctl {
   int skip_arrival_block = -1;            // test hook (-1 = off)
   int chunk_arcs = -1;                    // dynamic Atomic-Hook chunk (<= 0: one static slice per warp)
   int tile_w = 0;                         // hierarchical hook window (vertices; 0 = plain hook)
-  long long unit_arcs = 0;                // (unused by the two-phase hook)
   int2* wl = nullptr;                     // worklist of arcs left for the global hook
   unsigned long long wl_cap = 0;
   int* ovf_units = nullptr;               // windows whose worklist appends overflowed

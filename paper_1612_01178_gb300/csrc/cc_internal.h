@@ -23,7 +23,6 @@ struct Problem {
   int segments;
   bool sym;
   int tile_w;          // > 0: hierarchical hook with this window (CSR only)
-  long long unit_arcs; // hierarchical hook work unit
 };
 
 enum : int { kKindCsr = 1, kKindCoo = 2 };

@@ -220,6 +220,24 @@ def test_grid_4096_road(dev):
                                   want, f"{mode} sym={sym} tile={tile} s={segments}")
 
 
+def test_automatic_window_choice(dev):
+    """Automatic hook choice: the grid (ID locality) gets the two-phase hook (two launches) with a
+    balanced window, a multiple of 256 in [2048, 18432]; a randomly numbered R-MAT graph gets the
+    plain hook (one launch)."""
+    for g, tiled in ((gen.grid_csr(1500, 0.9, seed=11), True), (gen.rmat_csr(18, 8, seed=12), False)):
+        want = expect(g.row_ptr, g.col)
+        with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC) as cc:
+            out = cc.csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
+            info = cc.run_info()
+        assert_labels(out.cpu().numpy(), want, f"auto {g}")
+        W = info["tile_vertices"]
+        if tiled:
+            assert W % 256 == 0 and 2048 <= W <= 18432, info
+            assert info["launches"] == 2, info
+        else:
+            assert W == 0 and info["launches"] == 1, info
+
+
 def test_grid_small_percolation(dev):
     for p in (0.3, 0.5, 0.7, 1.0):
         g = gen.grid_csr(700, p, seed=9)

@@ -80,7 +80,11 @@ enum {
 
 /* How the segment loop of Fig. 4 is driven on the device. */
 typedef enum cc_mode {
-  CC_MODE_AUTO = 0,        /* choose per graph size (currently: persistent) */
+  CC_MODE_AUTO = 0,        /* CC_MODE_PERSISTENT, except that a symmetric CSR (CC_FLAG_SYMMETRIC) of at
+                              least 2^17 vertices with no ID locality and skewed degrees (at least a
+                              quarter of the sampled rows below a quarter of the mean degree, as in
+                              power-law graphs), with tile_vertices = 0, runs CC_MODE_FILTERED;
+                              cc_last_run_info reports the mode that ran */
   CC_MODE_PERSISTENT = 1,  /* one cooperative launch; phases separated by grid barriers */
   CC_MODE_MULTI_LAUNCH = 2, /* Fig. 4 as printed: one init, then Hook and Multi-Jump kernels per segment */
   /* The baselines the paper measures against (Section IV, Fig. 5), CSR only: the host loop of
@@ -88,7 +92,17 @@ typedef enum cc_mode {
      after every Hook round and every Jump (one CPU-GPU round trip each) ... */
   CC_MODE_SOMAN = 3,
   /* ... and the same loop with each Compress done by one Multi-Jump launch. */
-  CC_MODE_SOMAN_MULTIJUMP = 4
+  CC_MODE_SOMAN_MULTIJUMP = 4,
+  /* Sampled-and-filtered hook, CSR with CC_FLAG_SYMMETRIC only (else CC_ERR_INVALID_ARG): one
+     cooperative launch running Fig. 4 with two arc subsets picked for the edge filter. The first
+     2 arcs of every row are hooked, a Multi-Jump makes every tree a star, the root of the largest
+     star is estimated from 256 sampled vertices, and then only the rows of vertices outside that
+     star are read, their remaining arcs hooked in both directions (the reverse of a skipped arc
+     is in a row that is read, unless both ends already share the star); a final Multi-Jump. On a
+     graph with a giant component most arcs are never read. Without a star holding an eighth of
+     the sample, the second subset is every arc, hooked as in CC_MODE_PERSISTENT. `segments`,
+     `tile_vertices` do not apply. */
+  CC_MODE_FILTERED = 5
 } cc_mode;
 
 typedef struct cc_options {
@@ -114,8 +128,10 @@ typedef struct cc_options {
                           followed by a Multi-Jump. -1 = off: every arc is hooked on pi (Fig. 4
                           as printed). 0 = automatic: graphs of at least 2^17 vertices whose
                           sampled arcs mostly stay inside 16384-vertex windows use the two-phase
-                          hook; the sample is a small kernel plus a synchronisation on the first
-                          call for a given (row_ptr, col_idx, V, n_arcs), reused afterwards. */
+                          hook, with a window balanced over the co-resident CTAs (a multiple of
+                          256, at most 18432); the sample is a small kernel plus a
+                          synchronisation on the first call for a given (row_ptr, col_idx, V,
+                          n_arcs), reused afterwards. */
   int32_t reserved;    /* must be 0 */
   int64_t timeout_ns;  /* limit of every device-side wait; 0 = 2 s */
 } cc_options;

@@ -39,6 +39,7 @@ CC_MODE_PERSISTENT = 1
 CC_MODE_MULTI_LAUNCH = 2
 CC_MODE_SOMAN = 3
 CC_MODE_SOMAN_MULTIJUMP = 4
+CC_MODE_FILTERED = 5
 
 CC_INDEX_I32 = 4
 CC_INDEX_I64 = 8

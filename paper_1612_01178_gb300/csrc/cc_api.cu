@@ -39,6 +39,7 @@ struct cc_ctx {
   const void* auto_col = nullptr;
   long long auto_V = -1, auto_m = -1;
   int auto_w = 0;
+  bool auto_skewed = false;  // the sampled degrees are skewed (most rows far below the mean)
   // staging buffers of cc_labels_csr_host
   void* d_rp = nullptr;
   size_t d_rp_bytes = 0;
@@ -71,6 +72,11 @@ constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
 constexpr int kPhaseABlock = 1024; // default block of its phase-A launch
 constexpr int kSampleThreads = 16384;
 constexpr double kLocalFractionForTiles = 0.5;
+// Automatic choice of the sampled-and-filtered hook (CC_FLAG_SYMMETRIC, no locality): at least
+// this fraction of sampled rows has a degree below a quarter of the mean, as in power-law graphs
+// whose arcs sit mostly in the long rows of a giant component. (On R-MAT the filter skips most
+// arcs; on ER graphs, with no such skew, the first slice costs more than the plain hook.)
+constexpr double kLowDegreeFractionForFilter = 0.25;
 constexpr int kPhaseSlots = 64;
 
 // Makes `device` current for the scope of a call and restores the caller's device after.
@@ -121,28 +127,32 @@ int balanced_window(const cc_ctx* ctx, cc::Problem p, int block) {
 
 // Automatic hook choice (tile_vertices = 0): the two-phase hook pays off when most arcs join
 // vertices of the same window, i.e. when the vertex numbering has locality (meshes, road
-// networks in their natural order); otherwise the plain hook is used. A small sampling kernel
-// measures the fraction on the first call for a given graph (row_ptr, col_idx, V, n_arcs);
-// the answer is kept and reused while those stay the same. Only the speed depends on it.
-cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out) {
+// networks in their natural order); otherwise the plain hook is used, or, for a symmetric CSR
+// whose sampled degrees are skewed (*skewed_out), the sampled-and-filtered hook. A small
+// sampling kernel measures both on the first call for a given graph (row_ptr, col_idx, V,
+// n_arcs); the answers are kept and reused while those stay the same. Only the speed depends
+// on them.
+cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out, bool* skewed_out) {
   *w_out = 0;
+  *skewed_out = false;
   if (p.V < 2 * 65536) return CC_OK;  // small graphs: the plain hook
   const int w = window_for(p.V, kDefaultTileVertices);
   if (ctx->auto_rp == p.rp && ctx->auto_col == p.col && ctx->auto_V == p.V && ctx->auto_m == p.m) {
     *w_out = ctx->auto_w;
+    *skewed_out = ctx->auto_skewed;
     return CC_OK;
   }
   if (!ctx->d_sample) {
-    if (cudaMalloc(&ctx->d_sample, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_sample, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_sample, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_sample, 4 * sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       return CC_ERR_OOM;
     }
   }
-  cudaError_t e = cudaMemsetAsync(ctx->d_sample, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  cudaError_t e = cudaMemsetAsync(ctx->d_sample, 0, 4 * sizeof(unsigned long long), ctx->stream);
   if (e == cudaSuccess) e = cc::launch_sample_locality(p, w, ctx->d_sample, kSampleThreads, ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->h_sample, ctx->d_sample, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+    e = cudaMemcpyAsync(ctx->h_sample, ctx->d_sample, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "locality sample");
@@ -153,12 +163,15 @@ cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out) {
   ctx->auto_V = p.V;
   ctx->auto_m = p.m;
   ctx->auto_w = frac >= kLocalFractionForTiles ? w : 0;
+  const double rows = (double)ctx->h_sample[3];
+  ctx->auto_skewed = rows > 0 && (double)ctx->h_sample[2] / rows >= kLowDegreeFractionForFilter;
   *w_out = ctx->auto_w;
+  *skewed_out = ctx->auto_skewed;
   return CC_OK;
 }
 
 bool options_ok(const cc_options* o) {
-  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_SOMAN_MULTIJUMP) return false;
+  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_FILTERED) return false;
   if (o->segments < -1 || o->grid_blocks < 0) return false;
   if (o->chunk_arcs < -1 || (o->chunk_arcs > 0 && o->chunk_arcs % 32 != 0)) return false;
   if (o->tile_vertices != 0 && o->tile_vertices != -1 &&
@@ -301,6 +314,18 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   info.segments = p.segments;
   int mode = o.mode == CC_MODE_AUTO ? CC_MODE_PERSISTENT : o.mode;
   info.mode = mode;
+  p.filtered = false;
+  if (mode == CC_MODE_FILTERED) {
+    if (p.kind != cc::kKindCsr || !p.sym) {
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error),
+                    "CC_MODE_FILTERED needs CSR input with CC_FLAG_SYMMETRIC");
+      return CC_ERR_INVALID_ARG;
+    }
+    p.filtered = true;
+    p.segments = 2;  // the two arc subsets
+    info.segments = 2;
+    mode = CC_MODE_PERSISTENT;  // one cooperative launch, shaped like the persistent one
+  }
 
   info.block = block;
   if (o.flags & CC_FLAG_VALIDATE) {
@@ -313,13 +338,22 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   // Two-phase hierarchical hook (CSR, persistent mode): windows of W vertices.
   p.tile_w = 0;
   int w = 0;
-  if (p.kind == cc::kKindCsr && mode == CC_MODE_PERSISTENT && p.m > 0) {
+  if (p.kind == cc::kKindCsr && mode == CC_MODE_PERSISTENT && p.m > 0 && !p.filtered) {
     if (o.tile_vertices > 0) {
       w = window_for(p.V, o.tile_vertices);
     } else if (o.tile_vertices == 0) {
-      const cc_status st = auto_window(ctx, p, &w);
+      bool skewed = false;
+      const cc_status st = auto_window(ctx, p, &w, &skewed);
       if (st != CC_OK) return st;
-      if (w > 0) w = balanced_window(ctx, p, o.block > 0 ? o.block : kPhaseABlock);
+      if (w > 0) {
+        w = balanced_window(ctx, p, o.block > 0 ? o.block : kPhaseABlock);
+      } else if (skewed && p.sym && o.mode == CC_MODE_AUTO) {
+        // no locality, skewed degrees: the sampled-and-filtered hook (one cooperative launch)
+        p.filtered = true;
+        p.segments = 2;
+        info.segments = 2;
+        info.mode = CC_MODE_FILTERED;
+      }
     }
   }
   if (w > 0) {

@@ -760,6 +760,121 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Sampled-and-filtered hook (CSR with CC_FLAG_SYMMETRIC): Fig. 4 with two arc subsets chosen for
+// the edge filter. Slice 1 hooks the first kSampleArcs arcs of every row, a Multi-Jump makes every
+// tree a star, and the largest star is found from a sample of roots. Slice 2 then reads only the
+// rows of vertices outside that star and hooks their remaining arcs in both directions: an arc
+// (u, v) whose row u lies in the star is not read, because u is already joined to the star and
+// the reverse arc (v, u) is read from v's row unless v is in the star too (then u and v already
+// share a tree). Without a star of at least kGiantSamples / 8 sampled roots, slice 2 is the plain
+// hook of every arc.
+
+constexpr int kSampleArcs = 2;
+constexpr int kGiantSamples = 256;
+
+// Slice 1: the first kSampleArcs arcs of rows tid, tid + T, ..., hooked together.
+template <typename OffT>
+__device__ __forceinline__ void hook_row_heads(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                               int V, OffT nnz, long long tid, long long nthreads, const Ctl& c) {
+  for (long long x = tid; x < V; x += nthreads) {
+    const int u = (int)x;
+    OffT a0 = ld_ro(rp + u), a1 = ld_ro(rp + u + 1);
+    if (!(a0 >= 0 && a0 <= a1 && a1 <= nnz)) {
+      raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)u);
+      a1 = a0;
+    }
+    int uu[kSampleArcs], v[kSampleArcs];
+    bool live[kSampleArcs];
+#pragma unroll
+    for (int j = 0; j < kSampleArcs; ++j) {
+      const bool has = (long long)a0 + j < (long long)a1;
+      v[j] = has ? ld_stream(col + a0 + j) : 0;
+      const bool in_range = (unsigned)v[j] < (unsigned)V;
+      if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a0 + j);
+      live[j] = has && in_range && v[j] != u;
+      uu[j] = u;
+    }
+    atomic_hook_k<kSampleArcs>(pi, uu, v, live, V, c);
+  }
+}
+
+// The most frequent root among n = min(kGiantSamples, blockDim.x) vertices spread over [0, V),
+// if it holds at least one eighth of them, else -1. Called by one whole block after a Multi-Jump
+// (pi(x) is then x's root). Only the speed depends on the answer: slice 2 is correct for any
+// value, since a row is skipped only when its vertex's parent is that value.
+__device__ __forceinline__ int giant_root(const int* pi, int V) {
+  __shared__ int s_samples[kGiantSamples];
+  __shared__ unsigned long long s_best;
+  const int t = threadIdx.x;
+  const int n = blockDim.x < kGiantSamples ? (int)blockDim.x : kGiantSamples;
+  if (t == 0) s_best = 0ull;
+  if (t < n) {
+    const long long x = ((long long)t * (long long)V) / n + ((t * 40503) % 977) % (V / n + 1);
+    s_samples[t] = ld_pi(pi + (x < V ? x : V - 1));
+  }
+  __syncthreads();
+  if (t < n) {
+    const int mine = s_samples[t];
+    unsigned cnt = 0;
+    for (int j = 0; j < n; ++j) cnt += s_samples[j] == mine ? 1u : 0u;
+    atomicMax(&s_best, ((unsigned long long)cnt << 32) | (unsigned)mine);
+  }
+  __syncthreads();
+  const unsigned long long best = s_best;
+  return 8ull * (best >> 32) >= (unsigned long long)n ? (int)(best & 0xffffffffull) : -1;
+}
+
+// Slice 2: the arcs from position kSampleArcs on of every row whose vertex is not in the tree of
+// `giant`, both directions, one row per lane; rows of more than 32 such arcs are walked by the
+// whole warp, 32 arcs at a time.
+template <typename OffT>
+__device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                                  int V, OffT nnz, int giant, long long tid, long long nthreads,
+                                                  const Ctl& c) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = tid >> 5, nwarps = nthreads >> 5;
+  for (long long base = warp * 32; base < V; base += nwarps * 32) {  // warp-uniform
+    const long long x = base + lane;
+    const int u = (int)x;
+    long long a0 = 0, a1 = 0;
+    if (x < V && ld_pi(pi + u) != giant) {
+      a0 = (long long)ld_ro(rp + u);
+      a1 = (long long)ld_ro(rp + u + 1);
+      if (!(a0 >= 0 && a0 <= a1 && a1 <= (long long)nnz)) a1 = a0;  // reported by slice 1
+      a0 = a0 + kSampleArcs < a1 ? a0 + kSampleArcs : a1;
+    }
+    const bool heavy = a1 - a0 > 32;
+    if (!heavy) {
+      for (long long a = a0; a < a1; ++a) {
+        const int v = ld_stream(col + a);
+        if ((unsigned)v >= (unsigned)V) {
+          raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+          continue;
+        }
+        if (v != u) atomic_hook(pi, u, v, V, c);
+      }
+    }
+    unsigned hv = __ballot_sync(kFull, heavy);
+    while (hv) {
+      const int h = __ffs(hv) - 1;
+      hv &= hv - 1;
+      const int hu = __shfl_sync(kFull, u, h);
+      const long long h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
+      for (long long bb = h0; bb < h1; bb += 32) {
+        const long long a = bb + lane;
+        const bool has = a < h1;
+        const int v = has ? ld_stream(col + a) : 0;
+        const bool in_range = (unsigned)v < (unsigned)V;
+        if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+        const int uu[1] = {hu}, vv[1] = {v};
+        const bool live[1] = {has && in_range && v != hu};
+        atomic_hook_k<1>(pi, uu, vv, live, V, c);
+      }
+    }
+  }
+}
+
 // Bytes of dynamic shared memory of phase A for a block of `block` threads: the window's parent
 // array (W entries of lt_bytes each) followed by the per-warp scratch (worklist sink and queue
 // of deferred local hooks).

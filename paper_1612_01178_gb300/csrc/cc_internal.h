@@ -23,6 +23,7 @@ struct Problem {
   int segments;
   bool sym;
   int tile_w;          // > 0: hierarchical hook with this window (CSR only)
+  bool filtered;       // sampled-and-filtered hook (CSR with sym only)
 };
 
 enum : int { kKindCsr = 1, kKindCoo = 2 };
@@ -85,6 +86,7 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
 
 // Locality sample: out[0] += sampled arcs with both ends in one window of W vertices,
 // out[1] += sampled arcs (out must be zeroed by the caller).
+// out[2] += sampled rows whose degree is below a quarter of the mean, out[3] += sampled rows.
 cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* out, int threads, cudaStream_t stream);
 
 // Kernels of the host-driven loop of Fig. 1 (Soman et al.'s Hook-Compress with the Hook and

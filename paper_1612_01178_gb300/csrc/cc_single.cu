@@ -58,6 +58,46 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_csr_persistent(const OffT* __r
   phase_end(c);
 }
 
+// Sampled-and-filtered hook (CSR, CC_FLAG_SYMMETRIC), one cooperative launch: init pi; hook the
+// first kSampleArcs arcs of every row; Multi-Jump; estimate the largest star's root (block 0,
+// published in counters[3]); hook the remaining arcs of the rows outside that star (or, without
+// a large star, every arc with the plain hook); Multi-Jump.
+template <typename OffT>
+__global__ void __launch_bounds__(kMaxBlock, 2) k_csr_filtered(const OffT* __restrict__ rp,
+                                                               const int* __restrict__ col, int* pi, int V, OffT nnz,
+                                                               Ctl c) {
+  phase_start(c);
+  if (ld_relaxed(&c.st->error) == 0) {
+    unsigned epoch = 0;
+    const long long tid = global_tid(), nt = global_threads();
+    init_pi(pi, V, tid, nt);
+    bool go = grid_sync(c, epoch);
+    if (go) {
+      hook_row_heads<OffT>(rp, col, pi, V, nnz, tid, nt, c);
+      go = grid_sync(c, epoch);
+    }
+    if (go) {
+      multi_jump(pi, V, tid, nt, c);
+      go = grid_sync(c, epoch);
+    }
+    if (go) {
+      if (blockIdx.x == 0) {
+        const int g = giant_root(pi, V);
+        if (threadIdx.x == 0) c.st->counters[3] = (unsigned long long)(unsigned)g;
+      }
+      go = grid_sync(c, epoch);
+    }
+    if (go) {
+      const int g = (int)(unsigned)ld_volatile_u64(&c.st->counters[3]);
+      if (g >= 0) hook_rows_outside<OffT>(rp, col, pi, V, nnz, g, tid, nt, c);
+      else hook_csr_arcs<OffT, true>(rp, col, pi, V, (OffT)0, nnz, tid, nt, &c.st->counters[0], c);
+      go = grid_sync(c, epoch);
+    }
+    if (go) multi_jump(pi, V, tid, nt, c);
+  }
+  phase_end(c);
+}
+
 // Two-phase hierarchical hook, first launch: phase A (window-local hooks in shared memory, pi
 // written, worklist E' built). Windows are taken from a work counter, so the grid needs no
 // co-residency; at the default window two 1024-thread CTAs share an SM.
@@ -177,9 +217,13 @@ __global__ void __launch_bounds__(256) k_sample_locality(const OffT* __restrict_
                                                          int V, OffT nnz, int W, unsigned long long* out) {
   const long long t = global_tid(), T = global_threads();
   const int u = (int)((t * (long long)V) / T);
-  bool sampled = false, local = false;
+  bool sampled = false, local = false, row = false, low = false;
   if (u < V) {
     const OffT a0 = rp[u], a1 = rp[u + 1];
+    if (a0 >= 0 && a0 <= a1 && a1 <= nnz) {
+      row = true;
+      low = 4.0 * (double)(a1 - a0) * (double)V < (double)nnz;  // degree below a quarter of the mean
+    }
     if (a0 >= 0 && a0 < a1 && a1 <= nnz) {
       const int v = col[a0 + (a1 - a0) / 2];
       if ((unsigned)v < (unsigned)V && v != u) {
@@ -190,9 +234,15 @@ __global__ void __launch_bounds__(256) k_sample_locality(const OffT* __restrict_
   }
   const unsigned ns = __popc(__ballot_sync(kFull, sampled));
   const unsigned nl = __popc(__ballot_sync(kFull, local));
+  const unsigned nr = __popc(__ballot_sync(kFull, row));
+  const unsigned nlow = __popc(__ballot_sync(kFull, low));
   if ((threadIdx.x & 31) == 0 && ns) {
     atomicAdd(out, (unsigned long long)nl);
     atomicAdd(out + 1, (unsigned long long)ns);
+  }
+  if ((threadIdx.x & 31) == 0 && nr) {
+    atomicAdd(out + 2, (unsigned long long)nlow);
+    atomicAdd(out + 3, (unsigned long long)nr);
   }
 }
 
@@ -285,6 +335,8 @@ size_t phase_a_smem_bytes(const Problem& p, int block) {
 
 int persistent_blocks_per_sm(const Problem& p, int block) {
   if (p.kind == kKindCoo) return blocks_per_sm(k_coo_persistent, block, 0);
+  if (p.filtered)
+    return p.rp64 ? blocks_per_sm(k_csr_filtered<long long>, block, 0) : blocks_per_sm(k_csr_filtered<int>, block, 0);
   auto occ = [&](auto k) { return blocks_per_sm(k, block, 0); };
   return p.rp64 ? with_csr_persistent<long long>(p, occ) : with_csr_persistent<int>(p, occ);
 }
@@ -304,6 +356,13 @@ int stage_blocks_per_sm(const Problem& p, int block) {
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
   if (p.kind == kKindCoo)
     return launch_kernel(k_coo_persistent, s, 0, true, stream, p.src, p.dst, p.pi, p.V, p.m, p.segments, c);
+  if (p.filtered) {
+    if (p.rp64)
+      return launch_kernel(k_csr_filtered<long long>, s, 0, true, stream, static_cast<const long long*>(p.rp), p.col,
+                           p.pi, p.V, (long long)p.m, c);
+    return launch_kernel(k_csr_filtered<int>, s, 0, true, stream, static_cast<const int*>(p.rp), p.col, p.pi, p.V,
+                         (int)p.m, c);
+  }
   if (p.rp64) {
     const long long* rp = static_cast<const long long*>(p.rp);
     return p.sym ? launch_kernel(k_csr_persistent<long long, true>, s, 0, true, stream, rp, p.col, p.pi, p.V,

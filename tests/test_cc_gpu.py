@@ -222,9 +222,12 @@ def test_grid_4096_road(dev):
 
 def test_automatic_window_choice(dev):
     """Automatic hook choice: the grid (ID locality) gets the two-phase hook (two launches) with a
-    balanced window, a multiple of 256 in [2048, 18432]; a randomly numbered R-MAT graph gets the
-    plain hook (one launch)."""
-    for g, tiled in ((gen.grid_csr(1500, 0.9, seed=11), True), (gen.rmat_csr(18, 8, seed=12), False)):
+    balanced window, a multiple of 256 in [2048, 18432]; a randomly numbered R-MAT graph (skewed
+    degrees) gets the sampled-and-filtered hook and an ER graph the plain hook (one launch each)."""
+    cases = ((gen.grid_csr(1500, 0.9, seed=11), True, ccl.CC_MODE_PERSISTENT),
+             (gen.rmat_csr(18, 8, seed=12), False, ccl.CC_MODE_FILTERED),
+             (gen.er_csr(300_000, 3_000_000, seed=13), False, ccl.CC_MODE_PERSISTENT))
+    for g, tiled, mode in cases:
         want = expect(g.row_ptr, g.col)
         with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC) as cc:
             out = cc.csr(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
@@ -236,6 +239,7 @@ def test_automatic_window_choice(dev):
             assert info["launches"] == 2, info
         else:
             assert W == 0 and info["launches"] == 1, info
+        assert info["mode"] == mode, info
 
 
 def test_grid_small_percolation(dev):
@@ -390,10 +394,12 @@ def test_rmat26_full_size(dev):
     want = expect(g.row_ptr, g.col)
     rp = torch.from_numpy(g.row_ptr).to(dev)
     col = torch.from_numpy(g.col).to(dev)
-    for opts in (dict(), dict(segments=4)):
+    for opts in (dict(), dict(mode=ccl.CC_MODE_PERSISTENT, segments=4)):  # filtered (automatic), plain
         with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYMMETRIC | ccl.CC_FLAG_SYNC, **opts) as cc:
             got = cc.csr(rp, col).cpu().numpy()
+            info = cc.run_info()
         assert_labels(got, want, f"rmat26 {opts}")
+        assert info["mode"] == (ccl.CC_MODE_FILTERED if not opts else ccl.CC_MODE_PERSISTENT), info
     n_comp = int((want == np.arange(g.n_vertices)).sum())
     sizes = np.bincount(want)
     assert sizes.max() > g.n_vertices // 4 and n_comp > 1000  # one giant component plus many singletons

@@ -380,11 +380,13 @@ def run_batched(args, rank, world, local_rank):
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, dist)
 
-    # the same single-graph kernel run graph by graph (best per-graph hook choice, no sampling)
+    # the single-graph kernels run graph by graph, each graph kind with its best hook and no
+    # sampling: two-phase for grids, sampled-and-filtered for R-MAT, plain for ER
     rp_slices, col_slices, lab_slices, ctxs = [], [], [], {}
-    for kind in ("plain", "tiled"):
+    for kind in ("plain", "tiled", "filtered"):
         ctxs[kind] = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags,
-                                             tile_vertices=-1 if kind == "plain" else 16384)
+                                             tile_vertices={"plain": -1, "tiled": 16384, "filtered": 0}[kind],
+                                             mode=ccl.CC_MODE_FILTERED if kind == "filtered" else ccl.CC_MODE_AUTO)
     for g in range(b.n_graphs):
         v0, v1, a0, a1 = int(b.v_off[g]), int(b.v_off[g + 1]), int(b.a_off[g]), int(b.a_off[g + 1])
         rp_slices.append(rp[v0 + g: v1 + g + 1])
@@ -393,7 +395,7 @@ def run_batched(args, rank, world, local_rank):
 
     def by_graph_step():
         for g in range(b.n_graphs):
-            c2 = ctxs["tiled" if b.kinds[g] == "grid" else "plain"]
+            c2 = ctxs[{"grid": "tiled", "rmat": "filtered"}.get(b.kinds[g], "plain")]
             c2.csr(rp_slices[g], col_slices[g], lab_slices[g])
 
     timed(by_graph_step, 1)

@@ -101,7 +101,8 @@ typedef enum cc_mode {
      is in a row that is read, unless both ends already share the star); a final Multi-Jump. On a
      graph with a giant component most arcs are never read. Without a star holding an eighth of
      the sample, the second subset is every arc, hooked as in CC_MODE_PERSISTENT. `segments`,
-     `tile_vertices` do not apply. */
+     `tile_vertices` do not apply. Arcs that are never read are not range-checked: an endpoint
+     outside [0, V) in a skipped row goes unreported (CC_FLAG_VALIDATE checks every arc first). */
   CC_MODE_FILTERED = 5
 } cc_mode;
 

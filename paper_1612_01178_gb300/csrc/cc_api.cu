@@ -32,6 +32,8 @@ struct cc_ctx {
   size_t d_unit_start_n = 0;
   long long* d_chunk_start = nullptr;  // batched: chunk table of the windows hooked arc by arc
   size_t d_chunk_start_n = 0;
+  int* d_hint = nullptr;  // batched: giant-star root per graph
+  size_t d_hint_n = 0;
   // automatic hook choice: locality sample buffer and the last decision
   unsigned long long* d_sample = nullptr;
   unsigned long long* h_sample = nullptr;
@@ -621,7 +623,8 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   if (grow_buffer(&ctx->d_unit_start, &ctx->d_unit_start_n, (size_t)n_graphs + 1) != cudaSuccess ||
       grow_buffer(&ctx->d_wl, &ctx->d_wl_pairs, cap) != cudaSuccess ||
       grow_buffer(&ctx->d_ovf, &ctx->d_ovf_n, n_windows) != cudaSuccess ||
-      grow_buffer(&ctx->d_chunk_start, &ctx->d_chunk_start_n, n_windows + 2) != cudaSuccess) {
+      grow_buffer(&ctx->d_chunk_start, &ctx->d_chunk_start_n, n_windows + 2) != cudaSuccess ||
+      grow_buffer(&ctx->d_hint, &ctx->d_hint_n, (size_t)n_graphs + 1) != cudaSuccess) {
     std::snprintf(ctx->last_error, sizeof(ctx->last_error), "batched scratch allocation failed");
     return CC_ERR_OOM;
   }
@@ -639,6 +642,7 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   p.plain_units = ctx->d_ovf;
   p.plain_cap = (int)std::min<size_t>(std::min(ctx->d_ovf_n, ctx->d_chunk_start_n - 2), INT32_MAX);
   p.plain_chunk_start = ctx->d_chunk_start;
+  p.graph_hint = ctx->d_hint;
   p.sym = sym;
 
   cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
@@ -852,6 +856,7 @@ void cc_destroy(cc_ctx* ctx) {
     if (ctx->d_ovf) cudaFree(ctx->d_ovf);
     if (ctx->d_unit_start) cudaFree(ctx->d_unit_start);
     if (ctx->d_chunk_start) cudaFree(ctx->d_chunk_start);
+    if (ctx->d_hint) cudaFree(ctx->d_hint);
     if (ctx->d_sample) cudaFree(ctx->d_sample);
     if (ctx->h_sample) cudaFreeHost(ctx->h_sample);
     if (ctx->d_status) cudaFree(ctx->d_status);

@@ -47,6 +47,7 @@ struct Batch {
   int plain_cap;
   long long* plain_chunk_start;  // [plain_cap + 2] first chunk of each such window, then the chunk
                                  // size (filled by the kernel)
+  int* graph_hint;               // [n_graphs] giant-star root of each graph (filled by the kernel)
   int total_v;             // label arena size (batch-global IDs are below it)
   long long row_elems;     // descriptor mode: row-offset arena size
   long long arc_elems;     // descriptor mode: arc arena size
@@ -181,6 +182,97 @@ __device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
   return 2ll * nl * ui.vg >= (long long)ns * ((long long)ui.vg + ui.nrows);
 }
 
+// ----- the sampled-and-filtered hook of the windows without locality (symmetric batches) -----
+// Slice 1 hooks the first kSampleArcs arcs of every row of those windows; a Multi-Jump over their
+// vertices follows; then one warp per graph takes the most frequent root of 32 vertices spread
+// over the graph as its giant-star hint (or -1); slice 2 reads only the rows whose vertex's parent
+// is not the hint and hooks their remaining arcs in both directions. The single-graph argument
+// holds per graph (arcs never leave their graph, and one hint serves all of a graph's rows): the
+// reverse of a skipped arc is in a row that is read, unless both ends already share the star.
+// Only graphs all of whose windows are hooked this way are filtered (see kMixedGraph).
+
+// graph_hint value of a graph with a window hooked in phase A (never a vertex ID).
+constexpr int kMixedGraph = -2;
+
+// Rows [i0, i1) of window ui: the first kSampleArcs arcs of each, one row per thread.
+__device__ __forceinline__ void batched_row_heads(const Batch& b, const UnitInfo& ui, int i0, int i1, const Ctl& c) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int u = ui.w0 + i;
+    int a0 = ui.rp[u], a1 = ui.rp[u + 1];
+    if (!(a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz)) {
+      raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+      if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+      a1 = a0;
+    }
+    int uu[kSampleArcs], vv[kSampleArcs];
+    bool live[kSampleArcs];
+#pragma unroll
+    for (int j = 0; j < kSampleArcs; ++j) {
+      const bool has = (long long)a0 + j < (long long)a1;
+      const int v = has ? ld_stream(ui.col + a0 + j) : 0;
+      const bool in_range = (unsigned)v < (unsigned)ui.vg;
+      if (has && !in_range) {
+        raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+        if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+      }
+      live[j] = has && in_range && v != u;
+      uu[j] = ui.vbase + u;
+      vv[j] = ui.vbase + v;
+    }
+    atomic_hook_k<kSampleArcs>(b.labels, uu, vv, live, b.total_v, c);
+  }
+}
+
+// Rows [i0, i1) of window ui whose vertex's parent is not `hint`: their arcs from position
+// kSampleArcs on, both directions; one row per lane, rows of more than 32 such arcs by the warp.
+__device__ __forceinline__ void batched_rows_outside(const Batch& b, const UnitInfo& ui, int i0, int i1, int hint,
+                                                     const Ctl& c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int base = i0 + warp * 32; base < i1; base += nwarps * 32) {  // warp-uniform
+    const int i = base + lane;
+    const int u = ui.w0 + i;
+    int a0 = 0, a1 = 0;
+    if (i < i1 && ld_pi(b.labels + ui.vbase + u) != hint) {
+      a0 = ui.rp[u];
+      a1 = ui.rp[u + 1];
+      if (!(a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz)) a1 = a0;  // reported by slice 1
+      a0 = a1 - a0 > kSampleArcs ? a0 + kSampleArcs : a1;
+    }
+    const bool heavy = a1 - a0 > 32;
+    if (!heavy) {
+      for (int a = a0; a < a1; ++a) {
+        const int v = ld_stream(ui.col + a);
+        if ((unsigned)v >= (unsigned)ui.vg) {
+          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+          continue;
+        }
+        if (v != u) atomic_hook(b.labels, ui.vbase + u, ui.vbase + v, b.total_v, c);
+      }
+    }
+    unsigned hv = __ballot_sync(kFull, heavy);
+    while (hv) {
+      const int h = __ffs(hv) - 1;
+      hv &= hv - 1;
+      const int hu = __shfl_sync(kFull, u, h);
+      const int h0 = __shfl_sync(kFull, a0, h), h1 = __shfl_sync(kFull, a1, h);
+      for (long long bb = h0; bb < h1; bb += 32) {
+        const long long a = bb + lane;
+        const bool has = a < h1;
+        const int v = has ? ld_stream(ui.col + a) : 0;
+        const bool in_range = (unsigned)v < (unsigned)ui.vg;
+        if (has && !in_range) {
+          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+        }
+        const int uu[1] = {ui.vbase + hu}, vv[1] = {ui.vbase + v};
+        const bool live[1] = {has && in_range && v != hu};
+        atomic_hook_k<1>(b.labels, uu, vv, live, b.total_v, c);
+      }
+    }
+  }
+}
+
 template <bool SYM>
 __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ctl& c) {
   __shared__ long long s_warp_sums[32];
@@ -202,7 +294,10 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       const int g = base + threadIdx.x;
       const long long n = g < b.n_graphs ? units_of(graph_vertices(b, g, c), W) : 0;
       const long long incl = block_scan(n, s_warp_sums, &s_total);
-      if (g < b.n_graphs) b.unit_start[g + 1] = carry + incl;
+      if (g < b.n_graphs) {
+        b.unit_start[g + 1] = carry + incl;
+        b.graph_hint[g] = 0;  // set to kMixedGraph by phase A below
+      }
       carry += s_total;
     }
   }
@@ -251,6 +346,9 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
         else raise_error(c.st, kErrInternal, kSiteHookGuard, (long long)k);  // capacity is the window count
       }
     } else {
+      // A graph with a window hooked in phase A is not filtered: phase A drops the arcs with
+      // v < u of a symmetric CSR, leaving them to the reverse arcs, which the filter may skip.
+      if (threadIdx.x == 0 && !one_cta(ui, n_units)) b.graph_hint[ui.g] = kMixedGraph;
       if (ui.nnz <= 0x7fffffffLL)
         phase_a_window<int, SYM, int>(ui.rp, ui.col, ui.vg, (int)ui.nnz, ui.w0, ui.nrows, ui.vbase, lp, sink, &s_ovf,
                                  &s_bad, c);
@@ -284,10 +382,57 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     c.st->report[0] = n_pairs;
     c.st->report[1] = (unsigned long long)s2;
   }
-  // Chunk table of the windows hooked arc by arc (block 0): window j owns chunks
-  // [chunk_start[j], chunk_start[j + 1]) of chunk_start[n_plain + 1] arcs each; a window whose
-  // row offsets are inconsistent gets one chunk, which reports it.
-  if (n_plain > 0) {
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long pparts = split_factor(n_plain, gridDim.x);
+  if (SYM && n_plain > 0) {
+    // Sampled-and-filtered hook of the windows without locality: slice 1, then a Multi-Jump
+    // over their vertices, then the per-graph hints (slice 2 runs with the worklist below).
+    for (unsigned long long item = blockIdx.x; item < n_plain * pparts; item += gridDim.x) {
+      const UnitInfo ui = unit_info(b, b.plain_units[item / pparts], W);
+      const long long part = (long long)(item % pparts);
+      batched_row_heads(b, ui, split_point<int>(ui.nrows, (long long)pparts, part),
+                        split_point<int>(ui.nrows, (long long)pparts, part + 1), c);
+    }
+    if (!grid_sync(c, epoch)) return;
+    for (unsigned long long item = blockIdx.x; item < n_plain * pparts; item += gridDim.x) {
+      const UnitInfo ui = unit_info(b, b.plain_units[item / pparts], W);
+      const long long part = (long long)(item % pparts);
+      const int base = ui.vbase + ui.w0;
+      const int i1 = split_point<int>(ui.nrows, (long long)pparts, part + 1);
+      for (int i = split_point<int>(ui.nrows, (long long)pparts, part) + threadIdx.x; i < i1; i += blockDim.x) {
+        const int x = base + i;
+        const int p = ld_pi(b.labels + x);
+        if (p != x) jump_from(b.labels, x, p, ld_pi(b.labels + p), b.total_v, c);
+      }
+    }
+    if (!grid_sync(c, epoch)) return;
+    for (long long gw = tid >> 5; gw < b.n_graphs; gw += nt >> 5) {  // one warp per graph
+      const int gi = (int)gw;
+      const long long u0 = b.unit_start[gi], u1 = b.unit_start[gi + 1];
+      int hint = -1;
+      const int mark = b.graph_hint[gi];
+      if (mark == kMixedGraph) {
+        hint = kMixedGraph;  // matches no vertex: every row is read
+      } else if (u1 > u0) {
+        const UnitInfo ui = unit_info(b, u0, W);
+        if (!one_cta(ui, n_units)) {
+          const int x = ui.vbase + (int)(((long long)lane * ui.vg) / 32);
+          const int val = ld_pi(b.labels + x);
+          const unsigned grp = __match_any_sync(kFull, val);
+          const int best = __reduce_max_sync(kFull, (unsigned)((__popc(grp) << 5) | lane));
+          const int val_best = __shfl_sync(kFull, val, best & 31);
+          if ((best >> 5) >= 4) hint = val_best;  // at least an eighth of the 32 samples
+        }
+      }
+      if (lane == 0) b.graph_hint[gi] = hint;
+    }
+    if (!grid_sync(c, epoch)) return;
+  }
+  // Chunk table of the windows hooked arc by arc (block 0; batches without CC_FLAG_SYMMETRIC):
+  // window j owns chunks [chunk_start[j], chunk_start[j + 1]) of chunk_start[n_plain + 1] arcs
+  // each; a window whose row offsets are inconsistent gets one chunk, which reports it.
+  if (!SYM && n_plain > 0) {
     if (blockIdx.x == 0) {
       long long arcs = 0;
       for (unsigned long long j = threadIdx.x; j < n_plain; j += blockDim.x) {
@@ -320,13 +465,19 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     }
     if (!grid_sync(c, epoch)) return;
   }
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
   for (long long seg = 0; seg < s2; ++seg) {
     const unsigned long long p0 = split_point<unsigned long long>(n_pairs, s2, seg);
     const unsigned long long p1 = split_point<unsigned long long>(n_pairs, s2, seg + 1);
     hook_worklist(b.labels, c.wl, p0, p1, tid, nt, b.total_v, c);
-    if (seg == 0 && n_plain > 0) {  // windows without locality: every arc on pi, in chunks from a counter
+    if (SYM && seg == 0 && n_plain > 0) {  // slice 2 of the windows without locality
+      for (unsigned long long item = blockIdx.x; item < n_plain * pparts; item += gridDim.x) {
+        const UnitInfo ui = unit_info(b, b.plain_units[item / pparts], W);
+        const long long part = (long long)(item % pparts);
+        batched_rows_outside(b, ui, split_point<int>(ui.nrows, (long long)pparts, part),
+                             split_point<int>(ui.nrows, (long long)pparts, part + 1), b.graph_hint[ui.g], c);
+      }
+    }
+    if (!SYM && seg == 0 && n_plain > 0) {  // windows without locality: every arc on pi, in chunks from a counter
       const long long n_chunks = *reinterpret_cast<volatile long long*>(b.plain_chunk_start + n_plain);
       const long long chunk = *reinterpret_cast<volatile long long*>(b.plain_chunk_start + n_plain + 1);
       if (lane == 0) s_warp_bad[warp] = 0;
@@ -435,6 +586,7 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
   b.plain_units = p.plain_units;
   b.plain_cap = p.plain_cap;
   b.plain_chunk_start = p.plain_chunk_start;
+  b.graph_hint = p.graph_hint;
   b.total_v = (int)p.total_v;
   b.row_elems = p.row_elems;
   b.arc_elems = p.arc_elems;

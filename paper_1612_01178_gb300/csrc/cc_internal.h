@@ -76,6 +76,7 @@ struct BatchProblem {
   int* plain_units;
   int plain_cap;
   long long* plain_chunk_start;  // [plain_cap + 2] chunk table of plain_units and chunk size (kernel-filled)
+  int* graph_hint;               // [n_graphs] giant-star root per graph (kernel-filled, symmetric batches)
   long long total_v;    // label arena size
   long long row_elems;  // descriptor mode: arena sizes
   long long arc_elems;

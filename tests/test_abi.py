@@ -79,3 +79,15 @@ def test_no_cpu_fallback_in_the_product():
     for path in glob.glob(os.path.join(ROOT, "paper_1612_01178_gb300", "**", "*.py"), recursive=True):
         text = open(path).read()
         assert "import oracle" not in text and "from oracle" not in text, path
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/cc.h has the same value in the Python binding (status codes,
+    index types, flags, modes), and the binding defines no CC_ constant the header lacks."""
+    from paper_1612_01178_gb300 import cc
+    text = open(os.path.join(ROOT, "include", "cc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(CC_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    assert {"CC_OK", "CC_FLAG_SYMMETRIC", "CC_MODE_AUTO", "CC_MODE_FILTERED", "CC_INDEX_I64"} <= set(header)
+    binding = {k: v for k, v in vars(cc).items() if k.startswith("CC_") and isinstance(v, int)}
+    assert binding == header, (sorted(set(binding.items()) ^ set(header.items())))

@@ -159,3 +159,27 @@ def test_batched_argument_errors(dev):
                                      None) == ccapi.CC_ERR_INVALID_ARG
         assert lib.cc_labels_batched(cc.handle, 1, 1 << 31, 0, x.data_ptr(), x.data_ptr(), x.data_ptr(), None,
                                      x.data_ptr(), None) == ccapi.CC_ERR_INVALID_ARG
+
+
+def test_graph_mixing_local_and_random_windows(dev):
+    """One graph whose first half is a grid (windows with locality: phase A, which leaves arcs
+    with v < u to their reverse arcs) and whose second half is random (windows hooked arc by arc),
+    joined by a few edges, in a batch with more windows than CTAs: the filter must not skip rows
+    of such a graph. Also the random half alone (every window without locality: filtered)."""
+    side = 200
+    grid = gen.grid_csr(side, 0.9, seed=21)
+    n_grid = side * side
+    er = gen.er_csr(40_000, 160_000, seed=22)
+    src = [np.repeat(np.arange(n_grid), np.diff(grid.row_ptr)), n_grid + np.repeat(np.arange(40_000), np.diff(er.row_ptr))]
+    dst = [grid.col.astype(np.int64), n_grid + er.col.astype(np.int64)]
+    links = np.random.default_rng(23).integers(0, n_grid, 50)
+    src.append(links)
+    dst.append(n_grid + links % 40_000)
+    s = np.concatenate(src)
+    d = np.concatenate(dst)
+    rp, col = symmetric_csr(n_grid + 40_000, s, d, np.int32)
+    mixed = gen.CSR(n_grid + 40_000, rp, col, len(col) // 2, "grid+er")
+    b = gen.batch_from_graphs([mixed, er] + edge_case_graphs())
+    for tile in (256, 1024):
+        got, _ = run_batched(dev, b, tile_vertices=tile, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC)
+        assert_batch(got, b, what=f"mixed windows tile={tile}")

@@ -1,16 +1,19 @@
 """Benchmark of the GB300 connected-components library (adaptive Hook-Compress).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid|er|rmat] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat|er|grid|...] [--impl ours|reference]
 
 One step = one complete labelling of the workload graph (pi init, every Atomic-Hook
 segment and every Multi-Jump) through the C ABI, with the graph already resident in
 HBM. Between steps L2 is flushed by writing a 256 MiB buffer (outside the timed events).
-Prints ONE JSON line on rank 0.
+Prints ONE JSON line on rank 0. The single-graph line is the headline workload (default: the
+largest single-GPU graph, R-MAT scale 26); the other single-graph workloads (--subs) follow in
+its "sub_records", each parity-checked and timed the same way with its own roofline block.
 
 Workloads (seeded synthetic graphs, generated on the host before timing):
-  grid    : road-like 4096 x 4096 lattice, each edge kept with p = 0.9, int32 CSR (default)
-  er      : Erdos-Renyi, V = 100,000, 1,000,000 drawn edges, int32 CSR
   rmat    : R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), permuted IDs, int64 offsets
+            (default)
+  er      : Erdos-Renyi, V = 100,000, 1,000,000 drawn edges, int32 CSR
+  grid    : road-like 4096 x 4096 lattice, each edge kept with p = 0.9, int32 CSR
   batched : 4096 independent graphs, |V| log-uniform in [1e3, 1e6], family uniform over
             {ER avg degree 4..32, 2D grid p = 0.9, R-MAT edge factor 8}; one batched launch per step
             (metric: graphs/s), with the single-graph kernel run graph by graph timed beside it
@@ -41,7 +44,7 @@ import gen  # noqa: E402
 METRIC = "CC edges/sec and % of HBM roofline at 1 GB300"
 UNIT = "edges/s"
 FLUSH_BYTES = 256 << 20
-DEFAULT_PEAK_GBS = 6674.5  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+DEFAULT_PEAK_GBS = 6800.0  # fallback when MEASURED_PEAKS.json is absent (one earlier GB300 measurement)
 
 WORKLOADS = {
     "grid": ("grid4096_p0.9", lambda: gen.workload_grid_4096(seed=1)),
@@ -93,15 +96,17 @@ def kernel_sources_sha256() -> str:
 
 
 def recorded_traffic(workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources.
+    Returns (bytes or None, the record). A record captured on a smaller graph of the same family
+    carries the factor by which it was scaled to this workload (units processed)."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f).get(workload)
         if rec and rec.get("sources_sha256") == kernel_sources_sha256():
-            return int(rec["dram_bytes"])
+            return int(rec["dram_bytes"]), rec
     except Exception:
         pass
-    return None
+    return None, {}
 
 
 def algorithmic_bytes(g) -> int:
@@ -253,29 +258,55 @@ def run_reference(args, rank, world):
     if args.workload == "serve":
         return run_reference_serve(args)
     name, make = WORKLOADS[args.workload]
+    if args.workload == "rmat" and args.rmat_scale != 26:
+        name = "rmat%d_ef16" % args.rmat_scale
+        make = lambda: gen.rmat_csr(args.rmat_scale, 16, seed=1, offsets64=True)  # noqa: E731
     g = make()
     import oracle
-    rp64 = g.row_ptr.astype(np.int64)
+    rp64, col, sample = oracle_sample(g, name)
+    edges = (int(rp64[-1]) // 2) if rp64[-1] != g.nnz else g.n_edges
     for _ in range(args.warmup):
-        oracle.labels_uf_csr(rp64, g.col)
+        oracle.labels_uf_csr(rp64, col)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.labels_uf_csr(rp64, g.col)
+        oracle.labels_uf_csr(rp64, col)
         times.append(time.perf_counter() - t0)
     ms = 1000 * statistics.mean(times)
-    value = g.n_edges / (ms / 1000)
+    value = edges / (ms / 1000)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"whole {name} graph per step (union-find oracle, 1 thread)"},
+        "config": {"workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges,
+                   "row_ptr": str(g.row_ptr.dtype), "seed": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# Arcs per step of the reference arm: graphs with more arcs are sampled (the oracle on all 2^31 arcs
+# of R-MAT 26 takes about half a minute on one host thread, too long for 20 + 5 steps).
+REFERENCE_SAMPLE_ARCS = 1 << 27
+
+
+def oracle_sample(g, name):
+    """Input of one reference step: the whole graph, or for large graphs the arcs of the rows
+    [0, R) (all V vertices kept, the rows from R on empty) with R the first row at which
+    REFERENCE_SAMPLE_ARCS arcs are reached. Rows of the permuted R-MAT are in random order, so
+    the prefix is a uniform sample of its rows. Returns (int64 row_ptr, col, description)."""
+    rp64 = g.row_ptr.astype(np.int64)
+    if g.nnz <= REFERENCE_SAMPLE_ARCS:
+        return rp64, g.col, f"whole {name} graph per step (union-find oracle, 1 thread)"
+    R = int(np.searchsorted(rp64, REFERENCE_SAMPLE_ARCS))
+    cut = int(rp64[R])
+    rp_s = rp64.copy()
+    rp_s[R:] = cut
+    return rp_s, g.col[:cut], (f"per step: the arcs of rows [0, {R}) of {name} ({cut} of {g.nnz} arcs, all "
+                               f"{g.n_vertices} vertices), union-find oracle, 1 thread; value = sampled "
+                               f"edges (arcs / 2) per second")
 
 
 # ---------------------------------------------------------------------------------------- ours
@@ -668,30 +699,38 @@ def run_segsweep(args, rank, world, local_rank):
     return 0 if line["parity"] == "bit-exact" else 3
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    import paper_1612_01178_gb300 as ccl
+def kernel_name(info, g, ccl) -> str:
+    off = "int" if g.row_ptr.dtype == np.int32 else "int64"
+    if info["tile_vertices"]:
+        return "k_phase_a<%s,SYM> + k_phase_b<%s,SYM> (one labelling, both launches)" % (off, off)
+    if info["mode"] == ccl.CC_MODE_FILTERED:
+        return "k_csr_filtered<%s>" % off
+    if info["mode"] == ccl.CC_MODE_PERSISTENT and info.get("small"):
+        return "k_csr_small<%s,SYM>" % off
+    return "k_csr_persistent<%s,SYM>" % off
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    torch.cuda.set_device(local_rank)
+
+def hook_description(info, wl, ccl) -> str:
+    if info["tile_vertices"]:
+        return "two-phase (window %d), worklist %d arcs in %d segment(s)" % (info["tile_vertices"], *wl)
+    if info["mode"] == ccl.CC_MODE_FILTERED:
+        return "sampled-and-filtered (first 2 arcs per row, then the rows outside the largest star)"
+    return "plain (per-arc on pi)"
+
+
+def measure_single(args, ccl, torch, g, name, *, world, rank, local_rank, dist, cpu_budget, with_e2e,
+                   sample_clocks):
+    """One workload graph: parity of the timed launch configuration against the oracle, K timed
+    labellings (CUDA events on the context's stream, L2 flushed between them), the roofline
+    block, the oracle's rate on this host and, optionally, the end-to-end rate through the
+    host-buffer entry point. Returns the record (a dict) on every rank."""
     dev = torch.device("cuda", local_rank)
-    name, make = WORKLOADS[args.workload]
-    if args.workload == "rmat" and args.rmat_scale != 26:
-        name = "rmat%d_ef16" % args.rmat_scale
-        make = lambda: gen.rmat_csr(args.rmat_scale, 16, seed=1, offsets64=True)  # noqa: E731
-    t0 = time.perf_counter()
-    g = make()
-    gen_s = time.perf_counter() - t0
-
     stream = torch.cuda.Stream(device=dev)
     flags = ccl.CC_FLAG_SYMMETRIC
+    mode = {"persistent": ccl.CC_MODE_PERSISTENT, "multi": ccl.CC_MODE_MULTI_LAUNCH,
+            "filtered": ccl.CC_MODE_FILTERED, "auto": ccl.CC_MODE_AUTO}[args.mode]
     cc = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, segments=args.segments,
-                                 tile_vertices=args.tile,
-                                 mode={"persistent": ccl.CC_MODE_PERSISTENT,
-                                       "multi": ccl.CC_MODE_MULTI_LAUNCH, "filtered": ccl.CC_MODE_FILTERED,
-                                       "auto": ccl.CC_MODE_AUTO}[args.mode])
+                                 tile_vertices=args.tile, mode=mode)
     with torch.cuda.stream(stream):
         rp = torch.from_numpy(g.row_ptr).to(dev, non_blocking=False)
         col = torch.from_numpy(g.col).to(dev, non_blocking=False)
@@ -699,7 +738,7 @@ def run_ours(args, rank, world, local_rank):
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream.synchronize()
 
-    # correctness of this exact launch configuration against the oracle (rank 0 also times it)
+    # correctness of this exact launch configuration against the oracle
     cc.csr(rp, col, labels)
     cc.sync()
     gpu_labels = labels.cpu().numpy()
@@ -709,14 +748,12 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     parity = None
     if rank == 0:
+        rate, runs, ref = cpu_oracle_rate(g, budget_s=cpu_budget)
         if world == 1:
-            rate, runs, ref = cpu_oracle_rate(g, budget_s=args.cpu_budget)
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"whole {name} graph, {runs} run(s) of the union-find oracle on 1 host thread"}
-        else:
-            import oracle
-            ref, _ = oracle.labels_uf_csr(g.row_ptr.astype(np.int64), g.col)
         parity = "bit-exact" if np.array_equal(ref, gpu_labels) else "MISMATCH"
+        del ref
 
     def step():
         with torch.cuda.stream(stream):
@@ -732,22 +769,13 @@ def run_ours(args, rank, world, local_rank):
         step()
     cc.sync()
     torch.cuda.synchronize()
-
-    gpu_id = str(local_rank)
-    try:
-        uuid = torch.cuda.get_device_properties(dev).uuid
-        gpu_id = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
-    except Exception:
-        pass
-    if "CUDA_VISIBLE_DEVICES" in os.environ and gpu_id == str(local_rank):
-        gpu_id = os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]
-    sampler = ClockSampler(gpu_id)
-
+    sampler = ClockSampler(device_uuid(torch, dev, local_rank)) if sample_clocks else None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     events = []
     wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -756,21 +784,23 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - wall0
     if dist is not None:
         dist.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     cc.sync()  # raises if any timed launch reported a device error
     step_ms = [a.elapsed_time(b) for a, b in events]
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, dist)
     launches = info["launches"] * args.steps
+    # the timed labellings must still give the oracle's labels
+    if rank == 0 and parity == "bit-exact" and not np.array_equal(labels.cpu().numpy(), gpu_labels):
+        parity = "MISMATCH (timed launches)"
 
-    # end to end through the host-buffer entry point (pinned host inputs, labels read back)
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         pin_rp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
         pin_col = torch.from_numpy(g.col).pin_memory().numpy()
         pin_out = torch.empty(g.n_vertices, dtype=torch.int32).pin_memory().numpy()
         cc_host = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, segments=args.segments,
-                                          tile_vertices=args.tile)
+                                          tile_vertices=args.tile, mode=mode)
         for _ in range(max(1, args.warmup)):
             cc_host.csr_host(pin_rp, pin_col, pin_out)
         n_e2e = max(3, min(args.steps, 20))
@@ -788,62 +818,105 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
                "d2h_bytes_per_step": int(4 * g.n_vertices), "ms_per_step": 1000 * e2e_s,
                "labels_match": bool(e2e_ok)}
+        del pin_rp, pin_col, pin_out
 
-    if rank != 0:
-        cc.close()
-        return 0
     peak, peak_kind = measured_peaks()
     b_alg = algorithmic_bytes(g)
     achieved = b_alg / (ms / 1000) / 1e9
+    traffic, traffic_rec = recorded_traffic(name)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_source": peak_kind, "bytes_alg_per_launch": b_alg,
+            "kernel": kernel_name(info, g, ccl), "kernel_ms_mean": ms, "kernel_ms_min": min(step_ms)}
+    if traffic:
+        # DRAM bytes the kernels actually moved (ncu, same sources) over the live mean duration
+        roof["dram_achieved"] = traffic / (ms / 1000) / 1e9
+        roof["dram_frac"] = roof["dram_achieved"] / peak
+        roof["traffic_over_alg"] = traffic / b_alg
+        if traffic_rec.get("note"):
+            roof["traffic_note"] = traffic_rec["note"]
+    if info["mode"] == ccl.CC_MODE_FILTERED:
+        roof["note"] = ("the sampled-and-filtered hook never reads the arcs of rows inside the largest star after "
+                        "its first slice, so it moves fewer DRAM bytes than bytes_alg_per_launch: frac is B_alg / "
+                        "time as defined, dram_frac is the bandwidth it actually uses")
+    rec = {
+        "workload": name, "value": job_rate(g.n_edges, world, ms_max), "unit": UNIT, "ms_per_step": ms_max,
+        "config": {
+            "workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges,
+            "row_ptr": str(g.row_ptr.dtype), "seed": 1, "mode": args.mode, "segments": info["segments"],
+            "grid_blocks": info["grid_blocks"], "block": info["block"], "flags": "CC_FLAG_SYMMETRIC",
+            "hook": hook_description(info, wl, ccl),
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "parity": parity, "wall_s_timed": wall,
+    }
+    cc.close()
+    del rp, col, labels, flush
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1612_01178_gb300 as ccl
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    name, make = WORKLOADS[args.workload]
+    if args.workload == "rmat" and args.rmat_scale != 26:
+        name = "rmat%d_ef16" % args.rmat_scale
+        make = lambda: gen.rmat_csr(args.rmat_scale, 16, seed=1, offsets64=True)  # noqa: E731
+    t0 = time.perf_counter()
+    g = make()
+    gen_s = time.perf_counter() - t0
+    head = measure_single(args, ccl, torch, g, name, world=world, rank=rank, local_rank=local_rank, dist=dist,
+                          cpu_budget=args.cpu_budget, with_e2e=not args.no_e2e, sample_clocks=True)
+    head["config"]["generation_s"] = round(gen_s, 3)
+    del g
+
+    # the other single-graph configurations, each parity-checked and timed the same way
+    subs = []
+    for key in [s for s in args.subs.split(",") if s and s != args.workload]:
+        sname, smake = WORKLOADS[key]
+        sg = smake()
+        rec = measure_single(args, ccl, torch, sg, sname, world=world, rank=rank, local_rank=local_rank,
+                             dist=dist, cpu_budget=min(args.cpu_budget, 3.0), with_e2e=not args.no_e2e,
+                             sample_clocks=False)
+        subs.append(rec)
+        del sg
+
+    if rank != 0:
+        return 0
+    parity_all = [head["parity"]] + [s["parity"] for s in subs]
     line = {
         "metric": METRIC,
-        "value": job_rate(g.n_edges, world, ms_max),
+        "value": head["value"],
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_max,
+        "ms_per_step": head["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {
-            "workload": name, "n_vertices": g.n_vertices, "n_arcs": g.nnz, "n_edges": g.n_edges,
-            "row_ptr": str(g.row_ptr.dtype), "seed": 1, "mode": args.mode, "segments": info["segments"],
-            "grid_blocks": info["grid_blocks"], "block": info["block"], "flags": "CC_FLAG_SYMMETRIC",
-            "hook": ("two-phase (window %d), worklist %d arcs in %d segment(s)" % (info["tile_vertices"], *wl))
-            if info["tile_vertices"] else ("sampled-and-filtered (first 2 arcs per row, then the rows outside the "
-                                           "largest star)" if info["mode"] == ccl.CC_MODE_FILTERED
-                                           else "plain (per-arc on pi)"),
-            "l2": "flushed between steps (256 MiB write outside the timed events)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "generation_s": round(gen_s, 3),
-        },
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(name), "peak_source": peak_kind,
-                     "bytes_alg_per_launch": b_alg,
-                     "kernel": (("k_phase_a<%s,SYM> + k_phase_b<%s,SYM> (one labelling, both launches)"
-                                 if info["tile_vertices"] else
-                                 ("k_csr_filtered<%s>" if info["mode"] == ccl.CC_MODE_FILTERED else
-                                  "k_csr_persistent<%s,SYM>"))
-                                % ((("int" if g.row_ptr.dtype == np.int32 else "int64"),) *
-                                   (2 if info["tile_vertices"] else 1))),
-                     "kernel_ms_mean": ms, "kernel_ms_min": min(step_ms),
-                     **({"note": "the sampled-and-filtered hook never reads the arcs of rows inside the largest "
-                                 "star after its first slice, so its DRAM traffic (the traffic field, when "
-                                 "recorded) is below bytes_alg_per_launch; frac is B_alg / time as defined"}
-                        if info["mode"] == ccl.CC_MODE_FILTERED else {})},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "clocks": clocks,
-        "gpu_launches": launches,
-        "parity": parity,
-        "wall_s_timed": wall,
+        "config": head["config"],
+        "roofline": head["roofline"],
+        "cpu_baseline": head["cpu_baseline"],
+        "e2e": head["e2e"],
+        "clocks": head["clocks"],
+        "gpu_launches": head["gpu_launches"] + sum(s["gpu_launches"] for s in subs),
+        "gpu_launches_headline": head["gpu_launches"],
+        "parity": head["parity"],
+        "wall_s_timed": head["wall_s_timed"],
+        "sub_records": [{k: v for k, v in s.items() if k != "clocks"} for s in subs],
     }
     print(json.dumps(line), flush=True)
-    cc.close()
-    return 0 if parity == "bit-exact" else 3
+    return 0 if all(p == "bit-exact" for p in parity_all) else 3
 
 
 def main(argv=None):
@@ -853,7 +926,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serve", "ablation", "segsweep"],
-                    default="grid")
+                    default="rmat")
+    ap.add_argument("--subs", default="er,grid",
+                    help="single-graph workloads measured after the headline one, as sub-records of its line")
     ap.add_argument("--n-graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--rmat-scale", type=int, default=26, help="scale of the rmat workload (26 = the full size)")
     ap.add_argument("--rates", default="100,500,1000,2000,5000", help="serve: arrival rates (req/s)")

@@ -86,7 +86,7 @@ typedef enum cc_mode {
                               power-law graphs), with tile_vertices = 0, runs CC_MODE_FILTERED;
                               cc_last_run_info reports the mode that ran */
   CC_MODE_PERSISTENT = 1,  /* one cooperative launch; phases separated by grid barriers */
-  CC_MODE_MULTI_LAUNCH = 2, /* Fig. 4 as printed: one init, then Hook and Multi-Jump kernels per segment */
+  CC_MODE_MULTI_LAUNCH = 2, /* host-driven (Section III): one init, then a Hook and a Multi-Jump launch per segment */
   /* The baselines the paper measures against (Section IV, Fig. 5), CSR only: the host loop of
      Fig. 1 with the non-atomic Hook and the single Jump of Fig. 2, reading a device change flag
      after every Hook round and every Jump (one CPU-GPU round trip each) ... */
@@ -126,8 +126,8 @@ typedef struct cc_options {
                           in the same window of this many consecutive IDs in shared memory and
                           writes those stars to pi; the other arcs form a worklist E' that phase B
                           hooks on pi in s' = 2|E'|/|V| segments (or `segments` if set), each
-                          followed by a Multi-Jump. -1 = off: every arc is hooked on pi (Fig. 4
-                          as printed). 0 = automatic: graphs of at least 2^17 vertices whose
+                          followed by a Multi-Jump. -1 = off: every arc is hooked on pi, one
+                          segment after the other (Section III). 0 = automatic: graphs of at least 2^17 vertices whose
                           sampled arcs mostly stay inside 16384-vertex windows use the two-phase
                           hook, with a window balanced over the co-resident CTAs (a multiple of
                           256, at most 18432); the sample is a small kernel plus a
@@ -268,20 +268,24 @@ void cc_destroy(cc_ctx* ctx);
    running inside a device memory allocator or pool, plug-ins whose host owns all
    device memory, or real-time paths that must not allocate).
    It needs no context and calls no cudaMalloc/cudaFree or allocating routine. The
-   only scratch the persistent kernel needs beyond the caller's arrays (a 64-byte
-   grid-barrier counter and error word) lives in a static 256-byte device array
-   inside libcc.so, held on every GPU that loads the library until the process
-   exits; its size does not grow with the graph. The graph limits are those of
+   only scratch the persistent kernel needs beyond the caller's arrays (its 72-byte
+   status block: grid-barrier counter, work counters and error word) lives in a
+   static 256-byte device array inside libcc.so, held on every GPU that loads the
+   library until the process exits; its size does not grow with the graph. It runs
+   the plain Atomic-Hook in one cooperative launch with cc_labels_csr's default
+   segment plan and work split (the two-phase and filtered hooks of cc_labels_csr
+   need a worklist or a sampling buffer, which this entry point does not have). The graph limits are those of
    cc_labels_csr: n_vertices <= 2^31 - 1, and n_arcs <= 2^31 - 1 with int32
    offsets; anything larger, or any other flag than CC_FLAG_SYMMETRIC, returns
    CC_ERR_INVALID_ARG.
      row_ptr, col_idx, labels: device pointers as for cc_labels_csr, on the
        current device; stream: cudaStream_t (NULL = legacy default stream).
    The call issues on `stream`, waits for it, and returns the device status of
-   this call (CC_OK, CC_ERR_OUT_OF_RANGE, CC_ERR_TIMEOUT, ...). The first call on
-   a device looks up the scratch array's device address (cudaGetSymbolAddress,
-   once per device) and must therefore come before any stream capture on that
-   device. All calls share the scratch array, which keeps the last call's
+   this call (CC_OK, CC_ERR_OUT_OF_RANGE, CC_ERR_TIMEOUT, ...). Because it waits,
+   it cannot be issued on a stream that is being captured: such a call returns
+   CC_ERR_INVALID_ARG without touching the stream. The first call on a device
+   looks up the scratch array's device address (cudaGetSymbolAddress, once per
+   device), which must not happen during a stream capture on that device. All calls share the scratch array, which keeps the last call's
    contents; each call clears it before launching. Calls whose GPU work could
    overlap (unordered streams, or concurrent host threads) race on it and must
    not be issued. */

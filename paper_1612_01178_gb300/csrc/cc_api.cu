@@ -51,14 +51,43 @@ struct cc_ctx {
   size_t d_labels_bytes = 0;
 };
 
+namespace cc {
+
+// s of Section III-B: 2|E|/|V| = arcs per vertex, rounded, at least 1.
+static int paper_segments(long long arcs, long long V) {
+  if (V <= 0 || arcs <= 0) return 1;
+  const double s = std::floor((double)arcs / (double)V + 0.5);
+  return (int)std::max(1.0, std::min(s, 1.0e6));
+}
+
+// Segment count when the caller leaves it to the library (segments = 0). The segmentation
+// sweep of Fig. 6 repeated on GB300 (ER graphs of average degree 2..128, both drivers) puts the
+// fastest s at 1..4 for every degree, far below the paper's 2|E|/|V| (at degree 86 that choice
+// is 1.65x slower than s = 1): with root walks that halve paths as they go, intermediate
+// compresses rarely pay for their full O(V) pass. Only very sparse graphs gained from a few
+// segments (degree 2: s = 4, 1.1x to 2.5x over s = 1). segments = -1 selects the paper's s.
+int default_segments(long long arcs, long long V, int requested) {
+  if (requested > 0) return requested;
+  if (requested < 0) return paper_segments(arcs, V);
+  if (V <= 0 || arcs <= 0) return 1;
+  return (double)arcs / (double)V < 3.0 ? 4 : 1;
+}
+
+// Automatic work split of the plain hook: warps take chunks of kAutoChunkArcs arcs from a counter
+// when a segment holds at least that many arcs per warp of the launch (a fixed slice per warp
+// leaves the grid waiting on the slowest slice of a skewed graph); smaller segments use fixed
+// slices (-1).
+int auto_chunk_arcs(long long arcs_per_segment, long long warps) {
+  constexpr int kAutoChunkArcs = 2048;
+  return arcs_per_segment >= (long long)kAutoChunkArcs * warps ? kAutoChunkArcs : -1;
+}
+
+}  // namespace cc
+
 namespace {
 
 constexpr long long kDefaultTimeoutNs = 2000000000LL;
 constexpr int kDefaultChunkArcs = 0;  // automatic
-// Automatic work split of the plain hook: warps take chunks of kAutoChunkArcs arcs from a counter
-// when a segment holds at least that many arcs per warp (a fixed slice per warp leaves the
-// grid waiting on the slowest slice of a skewed graph); smaller segments use fixed slices.
-constexpr int kAutoChunkArcs = 2048;
 // Default window of the two-phase hook: single graphs use 16384 vertices (64 KB of 32-bit local
 // parents, two 1024-thread CTAs per SM); the batched kernel keeps whole graphs of up to 32768
 // vertices in one CTA.
@@ -186,26 +215,6 @@ bool options_ok(const cc_options* o) {
   return true;
 }
 
-// s of Section III-B: 2|E|/|V| = arcs per vertex, rounded, at least 1.
-int paper_segments(long long arcs, long long V) {
-  if (V <= 0 || arcs <= 0) return 1;
-  const double s = std::floor((double)arcs / (double)V + 0.5);
-  return (int)std::max(1.0, std::min(s, 1.0e6));
-}
-
-// Segment count when the caller leaves it to the library (segments = 0). The segmentation
-// sweep of Fig. 6 repeated on GB300 (ER graphs of average degree 2..128, both drivers) puts the
-// fastest s at 1..4 for every degree, far below the paper's 2|E|/|V| (at degree 86 that choice
-// is 1.65x slower than s = 1): with root walks that halve paths as they go, intermediate
-// compresses rarely pay for their full O(V) pass. Only very sparse graphs gained from a few
-// segments (degree 2: s = 4, 1.1x to 2.5x over s = 1). segments = -1 selects the paper's s.
-int default_segments(long long arcs, long long V, int requested) {
-  if (requested > 0) return requested;
-  if (requested < 0) return paper_segments(arcs, V);
-  if (V <= 0 || arcs <= 0) return 1;
-  return (double)arcs / (double)V < 3.0 ? 4 : 1;
-}
-
 cc_status read_and_clear_status(cc_ctx* ctx) {
   cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(cc::DevStatus), cudaMemcpyDeviceToHost,
                                   ctx->stream);
@@ -256,8 +265,9 @@ cc_status flag_round(cc_ctx* ctx, F&& launch, bool* changed, cc_run_info* info) 
   return CC_OK;
 }
 
-// Fig. 1 driven from the host: repeat { Hook all arcs; Compress } until the Hook changes
-// nothing. Compress is a single Jump repeated until it changes nothing, or one Multi-Jump.
+// The host-driven loop of the Hook-Compress baseline (Section II): repeat { Hook all arcs;
+// Compress } until a Hook round changes nothing, each decision read back from the device
+// change flag. Compress is a single Jump repeated until it changes nothing, or one Multi-Jump.
 cc_status run_host_loop(cc_ctx* ctx, const cc::Problem& p, const cc::Ctl& c, cc::LaunchShape s, bool multijump,
                         cc_run_info* info) {
   cudaError_t e = cc::launch_init_only(p, c, s, ctx->stream);
@@ -298,7 +308,7 @@ cc_status run_host_loop(cc_ctx* ctx, const cc::Problem& p, const cc::Ctl& c, cc:
 cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   const cc_options& o = ctx->opt;
   int block = o.block > 0 ? o.block : kPlainBlock;
-  p.segments = default_segments(p.m, p.V, o.segments);
+  p.segments = cc::default_segments(p.m, p.V, o.segments);
   if (p.m == 0) p.segments = 1;
 
   cc::Ctl c;
@@ -394,8 +404,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     cc::LaunchShape s{(int)grid, block};
     if (o.chunk_arcs == 0) {
       const long long warps = grid * (block / 32);
-      const long long per_segment = p.m / std::max(1, p.segments);
-      c.chunk_arcs = per_segment >= (long long)kAutoChunkArcs * warps ? kAutoChunkArcs : -1;
+      c.chunk_arcs = cc::auto_chunk_arcs(p.m / std::max(1, p.segments), warps);
     }
     c.skip_arrival_block = ctx->skip_arrival_block;
     ctx->skip_arrival_block = -1;
@@ -592,7 +601,7 @@ cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const 
   p.sym = false;
   cc_options saved = ctx->opt;
   // Section III-B counts |E| edges: a COO edge stands for two arcs.
-  ctx->opt.segments = default_segments(2 * n_edges, n_vertices, ctx->opt.segments);
+  ctx->opt.segments = cc::default_segments(2 * n_edges, n_vertices, ctx->opt.segments);
   cc_status st = run_problem(ctx, p);
   ctx->opt = saved;
   return st;

@@ -32,7 +32,7 @@ struct DevStatus {
   int error_where;
   long long error_info;
 };
-constexpr size_t kPerLaunchStatusBytes = 56;  // bar, pad0, counters, report
+constexpr size_t kPerLaunchStatusBytes = 56;  // bar, changed, counters, report
 
 // Where an error was raised (DevStatus::error_where).
 enum ErrorSite : int {

@@ -40,6 +40,14 @@ int stage_blocks_per_sm(const Problem& p, int block);
 // Blocks of the phase-A kernel of the hierarchical hook per SM, with its window in shared memory.
 int phase_a_blocks_per_sm(const Problem& p, int block);
 
+// Segment plan of Fig. 4 (Section III-B): requested > 0 = exactly that many segments; -1 = the
+// paper's s = max(1, round(arcs / V)); 0 = this library's default from the segmentation sweep on
+// GB300 (s = 4 below an average degree of 3, else 1).
+int default_segments(long long arcs, long long V, int requested);
+// Automatic work split of the plain hook for a launch of `warps` warps: the chunk size (arcs)
+// warps take from a counter, or -1 for one fixed slice of the segment per warp.
+int auto_chunk_arcs(long long arcs_per_segment, long long warps);
+
 // One cooperative launch running init + all segments (Hook, barrier, Multi-Jump, barrier).
 cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 
@@ -47,7 +55,8 @@ cudaError_t launch_persistent(const Problem& p, const Ctl& c, LaunchShape s, cud
 // then the cooperative phase-B launch (shape sb: worklist segments, each with a Multi-Jump).
 cudaError_t launch_two_phase(const Problem& p, const Ctl& c, LaunchShape sa, LaunchShape sb, cudaStream_t stream);
 
-// Fig. 4 as printed: init, then per segment one Hook launch and one Multi-Jump launch.
+// The adaptive method of Section III driven by the host: init, then per segment one Hook launch
+// and one Multi-Jump launch.
 // Returns the number of launches issued in *launches.
 cudaError_t launch_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream, int* launches);
 

@@ -4,8 +4,8 @@
 // memory pool (which must not re-enter the allocator), plug-ins of hosts that own all device
 // memory and forbid others from allocating, and tight real-time paths that must not pay for
 // (or fail in) an allocation. This entry point needs no context. Its only scratch memory, the
-// grid-barrier counter and error word that the persistent kernel needs beyond the caller's
-// input and output arrays, lives in the file-scope device array below.
+// status block (grid-barrier counter, work counters, error word) that the persistent kernel
+// needs beyond the caller's input and output arrays, lives in the file-scope device array below.
 //
 // The array is allocated when the library is loaded and stays allocated on every GPU that
 // loads the library until the process exits. Every call shares it and it keeps the last
@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = 256;  // the stated maximum: one status block (64 bytes used)
+constexpr size_t kScratchBytes = 256;  // the stated maximum: one status block (sizeof(DevStatus) = 72 bytes used)
 static_assert(sizeof(cc::DevStatus) <= kScratchBytes, "status block must fit the static scratch");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -80,6 +80,14 @@ extern "C" cc_status cc_labels_csr_noalloc(int64_t n_vertices, int64_t n_arcs, c
     return CC_ERR_CUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The call reads its status back and waits for the stream, which a capturing stream does not
+  // allow: refuse before touching the stream, so the caller's capture stays valid.
+  cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap_status) != cudaSuccess) {
+    cudaGetLastError();
+    return CC_ERR_CUDA;
+  }
+  if (cap_status != cudaStreamCaptureStatusNone) return CC_ERR_INVALID_ARG;
 
   cc::Problem p{};
   p.kind = cc::kKindCsr;
@@ -90,9 +98,8 @@ extern "C" cc_status cc_labels_csr_noalloc(int64_t n_vertices, int64_t n_arcs, c
   p.V = (int)n_vertices;
   p.m = n_arcs;
   p.sym = (flags & CC_FLAG_SYMMETRIC) != 0;
-  const double avg = n_arcs > 0 ? (double)n_arcs / (double)n_vertices : 0.0;
-  p.segments = avg < 1.5 ? 1 : (int)(avg + 0.5);
-  if (p.segments > 1000000) p.segments = 1000000;
+  // the same segment plan as cc_labels_csr with default options
+  p.segments = n_arcs > 0 ? cc::default_segments(n_arcs, n_vertices, 0) : 1;
 
   const int block = 256;
   const int per_sm = cc::persistent_blocks_per_sm(p, block);
@@ -110,6 +117,7 @@ extern "C" cc_status cc_labels_csr_noalloc(int64_t n_vertices, int64_t n_arcs, c
   c.st = scratch;
   c.timeout_ns = 2000000000LL;
   c.skip_arrival_block = -1;
+  c.chunk_arcs = cc::auto_chunk_arcs(n_arcs / p.segments, grid * (block / 32));
 
   // The scratch keeps the previous call's barrier count and error word: clear them first.
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(cc::DevStatus), s);

@@ -1,6 +1,6 @@
 // Single-graph kernels: the persistent driver of Fig. 4 (one cooperative launch, grid
 // barriers between Hook and Multi-Jump phases), the two launches of the hierarchical hook, and
-// the per-phase kernels of the printed host loop, for CSR (int32 / int64 offsets, plain or
+// the per-phase kernels of a host-driven loop (one launch per Hook and per Multi-Jump), for CSR (int32 / int64 offsets, plain or
 // symmetrised) and COO inputs.
 #include "cc_internal.h"
 

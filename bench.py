@@ -522,6 +522,9 @@ def serve_pool(n: int, seed: int = 1):
 
 
 def run_serve(args, rank, world, local_rank):
+    """Continuous batching vs one request at a time on the same Poisson streams. Each request
+    copies its pool graph in from pinned host memory and its labels out into a pinned buffer of
+    that pool graph (requests of one graph in flight at once write identical labels there)."""
     import torch
     from paper_1612_01178_gb300.serve import Request, SequentialServer, Server, latency_summary
 
@@ -530,11 +533,12 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     t0 = time.perf_counter()
     graphs = serve_pool(args.pool, seed=1)
-    pinned = [(torch.from_numpy(g.row_ptr).pin_memory().numpy(), torch.from_numpy(g.col).pin_memory().numpy())
-              for g in graphs]
+    pinned = [(torch.from_numpy(g.row_ptr).pin_memory().numpy(), torch.from_numpy(g.col).pin_memory().numpy(),
+               torch.empty(g.n_vertices, dtype=torch.int32).pin_memory().numpy()) for g in graphs]
     gen_s = time.perf_counter() - t0
     budget = Server.budget_from_free_memory(0.4, local_rank, avg_degree=20.0)
-    srv = Server(local_rank, max_batch=args.max_batch, **budget)
+    lane_counts = [int(x) for x in args.lanes.split(",")]
+    servers = {n: Server(local_rank, max_batch=args.max_batch, lanes=n, **budget) for n in lane_counts}
     seq = SequentialServer(local_rank)
     rng = np.random.default_rng(7)
     rates = [float(r) for r in args.rates.split(",")]
@@ -542,46 +546,66 @@ def run_serve(args, rank, world, local_rank):
     def stream(rate, n):
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
         pick = rng.integers(0, len(graphs), n)
-        return [Request(i, float(arrivals[i]), *pinned[pick[i]]) for i in range(n)], pick
+        return arrivals, pick
 
-    # warm-up: every pool graph once through both servers; the labels are checked against the
+    def requests(arrivals, pick):
+        return [Request(i, float(arrivals[i]), *pinned[pick[i]]) for i in range(len(pick))]
+
+    # warm-up: every pool graph once through every server; the labels are checked against the
     # oracle and then serve as the expected answer of every later request for that graph
     import oracle
-    warm = [Request(i, 0.0, *pinned[i]) for i in range(len(graphs))]
-    srv.run(warm)
-    seq.run([Request(r.rid, 0.0, r.row_ptr, r.col) for r in warm])
-    expect = [r.labels.copy() for r in warm]
+    expect = [oracle.labels_uf_csr(g.row_ptr, g.col)[0] for g in graphs]
     parity = "bit-exact"
-    for i, g in enumerate(graphs):
-        if not np.array_equal(expect[i], oracle.labels_uf_csr(g.row_ptr, g.col)[0]):
-            parity = "MISMATCH (graph %d)" % i
+    warm_idx = np.arange(len(graphs))
+    for name, srv in list(servers.items()) + [("seq", seq)]:
+        out = srv.run(requests(np.zeros(len(graphs)), warm_idx))
+        for r in out:
+            if r.status != 0 or not np.array_equal(r.labels, expect[r.rid]):
+                parity = "MISMATCH (warm-up, %s, graph %d)" % (name, r.rid)
     results = []
     sampler = ClockSampler(device_uuid(torch, torch.device("cuda", local_rank), local_rank))
     sampler.start()
     for rate in rates:
         n = int(min(args.max_requests, max(args.min_requests, rate * args.seconds)))
-        reqs, pick = stream(rate, n)
-        out = srv.run(reqs)
-        s = latency_summary(out)
-        same = all(np.array_equal(r.labels, expect[i]) for r, i in zip(out, pick))
-        base = [Request(r.rid, r.arrival, r.row_ptr, r.col) for r in reqs]
-        b = latency_summary(seq.run(base))
-        if not same:
-            parity = "MISMATCH (continuous batching at %g req/s)" % rate
-        results.append({"rate_req_s": rate, "requests": n, "continuous_batching": s, "one_at_a_time": b,
-                        "batches": len(srv.batches), "mean_batch": n / max(1, len(srv.batches))})
-        srv.batches.clear()
+        row = {"rate_req_s": rate, "requests": n, "repeats": args.repeats}
+        for name in list(servers) + ["seq"]:
+            reps = []
+            for rep in range(args.repeats):
+                arrivals, pick = stream(rate, n)
+                srv = seq if name == "seq" else servers[name]
+                if name != "seq":
+                    srv.batches.clear()
+                out = srv.run(requests(arrivals, pick))
+                s = latency_summary(out)
+                if name != "seq":
+                    s["batches"] = len(srv.batches)
+                    s["mean_batch"] = n / max(1, len(srv.batches))
+                reps.append(s)
+                if not all(r.status == 0 and np.array_equal(r.labels, expect[i]) for r, i in zip(out, pick)):
+                    parity = "MISMATCH (%s at %g req/s)" % (name, rate)
+            key = "one_at_a_time" if name == "seq" else f"continuous_batching_lanes{name}"
+            row[key] = {"p50_ms": statistics.median(x["p50_ms"] for x in reps),
+                        "p99_ms": statistics.median(x["p99_ms"] for x in reps),
+                        "p99_ms_repeats": [x["p99_ms"] for x in reps],
+                        "throughput_req_s": statistics.median(x["throughput_req_s"] for x in reps),
+                        "device_p50_ms": statistics.median(x["device_p50_ms"] for x in reps),
+                        **({"mean_batch": statistics.median(x["mean_batch"] for x in reps)} if name != "seq" else {})}
+        results.append(row)
     clocks = sampler.stop()
-    srv.close()
+    for srv in servers.values():
+        srv.close()
     seq.close()
     ref = next((x for x in results if x["rate_req_s"] == 1000.0), results[len(results) // 2])
+    head = f"continuous_batching_lanes{lane_counts[0]}"
     line = {
-        "metric": "served p50/p99 latency", "value": ref["continuous_batching"]["p99_ms"], "unit": "ms (p99)",
+        "metric": "served p50/p99 latency", "value": ref[head]["p99_ms"], "unit": "ms (p99)",
         "n_gpus": 1, "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "serve", "pool_graphs": len(graphs), "rates": rates, "arena_elems": budget,
-                   "max_batch": args.max_batch, "flags": "CC_FLAG_SYMMETRIC", "generation_s": round(gen_s, 1),
-                   "value_is": "p99 latency at %g req/s" % ref["rate_req_s"]},
+                   "max_batch": args.max_batch, "lanes": lane_counts, "flags": "CC_FLAG_SYMMETRIC",
+                   "generation_s": round(gen_s, 1),
+                   "value_is": "p99 latency at %g req/s, %d lane(s), median of %d repeats"
+                               % (ref["rate_req_s"], lane_counts[0], args.repeats)},
         "rates": results, "clocks": clocks, "parity": parity,
     }
     print(json.dumps(line), flush=True)
@@ -937,6 +961,8 @@ def main(argv=None):
     ap.add_argument("--min-requests", type=int, default=150)
     ap.add_argument("--max-requests", type=int, default=3000)
     ap.add_argument("--max-batch", type=int, default=1024)
+    ap.add_argument("--lanes", default="2,1", help="serve: compute lanes of the servers compared (first = headline)")
+    ap.add_argument("--repeats", type=int, default=3, help="serve: Poisson streams per rate and server")
     ap.add_argument("--mode", choices=["auto", "persistent", "multi", "filtered"], default="auto",
                     help="auto = the library's automatic choice (two-phase, filtered or plain hook)")
     ap.add_argument("--segments", type=int, default=0, help="0 = the average degree (Section III-B)")

@@ -30,11 +30,17 @@
  *     edges are allowed. n_vertices = 0 and zero arcs are legal.
  *   - Calls are asynchronous and ordered on the context's stream unless
  *     CC_FLAG_SYNC is set. Argument errors are returned at once. Errors found
- *     on the device (an endpoint outside [0, V), a wait that ran out, a failed
- *     guard) are sticky in the context's device status word and are returned
- *     by cc_sync (or by the call itself with CC_FLAG_SYNC), which also clears
- *     them. While an error is pending, later device work of the same context
- *     exits early. Device code never traps.
+ *     on the device are sticky in the context's device status block and are
+ *     returned by cc_sync (or by the call itself with CC_FLAG_SYNC), which also
+ *     clears them. They come in two kinds:
+ *       - malformed input (CC_ERR_OUT_OF_RANGE: an endpoint outside [0, V),
+ *         offsets inconsistent with n_arcs): the bad arc or row is skipped and
+ *         reported, the call runs to its end (in a batch, every other graph is
+ *         labelled normally) and later calls are not affected; the labels of
+ *         the graph concerned are unspecified;
+ *       - fatal (CC_ERR_TIMEOUT, CC_ERR_INTERNAL): while one is pending, later
+ *         device work of the same context exits early.
+ *     Device code never traps.
  *   - A context is used by one host thread at a time.
  */
 #ifndef CC_H_
@@ -52,7 +58,7 @@ typedef struct cc_ctx cc_ctx;
 typedef enum cc_status {
   CC_OK = 0,
   CC_ERR_INVALID_ARG = 1,  /* bad argument detected on the host (sizes, null pointers, types) */
-  CC_ERR_OUT_OF_RANGE = 2, /* device: an endpoint outside [0, V), or (CC_FLAG_VALIDATE) bad offsets */
+  CC_ERR_OUT_OF_RANGE = 2, /* device, malformed input: an endpoint outside [0, V) or bad offsets */
   CC_ERR_OOM = 3,          /* a context-owned allocation failed */
   CC_ERR_CUDA = 4,         /* a CUDA runtime call failed; see cc_last_error_message */
   CC_ERR_TIMEOUT = 5,      /* device: a grid-wide wait exceeded cc_options.timeout_ns */
@@ -68,8 +74,9 @@ enum {
      are skipped, halving the hooks without changing any label. */
   CC_FLAG_SYMMETRIC = 1,
   /* Check offsets (row_ptr[0] = 0, non-decreasing, row_ptr[V] = n_arcs) and
-     endpoints on the device before hooking. Endpoints are always range-checked
-     while hooking; this adds the offset checks. */
+     endpoints on the device before hooking; if a check fails the call reports
+     CC_ERR_OUT_OF_RANGE and does not hook at all. Endpoints are always
+     range-checked while hooking; this adds the offset checks. */
   CC_FLAG_VALIDATE = 2,
   /* Block until the device work of the call is done and return its status. */
   CC_FLAG_SYNC = 4,
@@ -133,7 +140,9 @@ typedef struct cc_options {
                           256, at most 18432); the sample is a small kernel plus a
                           synchronisation on the first call for a given (row_ptr, col_idx, V,
                           n_arcs), reused afterwards. */
-  int32_t reserved;    /* must be 0 */
+  int32_t sm_limit;    /* > 0: the launches of this context fill at most this many SMs' worth of
+                          co-resident blocks (a share of the GPU, so that the launches of several
+                          contexts on different streams run side by side); 0 = all SMs */
   int64_t timeout_ns;  /* limit of every device-side wait; 0 = 2 s */
 } cc_options;
 
@@ -148,6 +157,15 @@ cc_status cc_create(cc_ctx** out, int device, void* stream, const cc_options* op
 /* Replaces the stream / options of a context. */
 cc_status cc_set_stream(cc_ctx* ctx, void* stream);
 cc_status cc_set_options(cc_ctx* ctx, const cc_options* opt);
+
+/* Per-call input status without a synchronisation (the paper has one graph per call and no
+   failure reporting; this serves a caller that keeps several calls in flight on one context,
+   such as a serving loop). With device_status a device int32 pointer, every following
+   labelling call of the context first sets *device_status = 0 on the context's stream, and
+   its kernels set it to CC_ERR_OUT_OF_RANGE if they find malformed input; read it after the
+   call's work (stream order). NULL turns the output off. The pointer is the caller's and must
+   stay valid while calls use it; the sticky status of the context is kept as well. */
+cc_status cc_set_launch_status(cc_ctx* ctx, int32_t* device_status);
 
 /* Connected components of a CSR graph (Fig. 4 over the arcs of the CSR).
  *   n_vertices  V >= 0.
@@ -182,7 +200,10 @@ cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const 
  *   labels_cat       device int32 [total_vertices], output: graph g's labels at v_off[g],
  *                    graph-local minimum vertex IDs.
  *   graph_status     device int32 [n_graphs] or NULL: set to CC_OK, or to
- *                    CC_ERR_OUT_OF_RANGE for a graph with an endpoint outside [0, V_g).
+ *                    CC_ERR_OUT_OF_RANGE for a graph with an endpoint outside [0, V_g) or
+ *                    inconsistent offsets. Such a graph's labels are unspecified; every other
+ *                    graph of the batch is labelled normally (the context's status reports
+ *                    CC_ERR_OUT_OF_RANGE as well).
  * total_vertices must be below 2^31 (labels are computed with batch-global IDs); each graph
  * must have fewer than 2^31 arcs. Graphs of at most tile_vertices vertices (default 32768)
  * are labelled inside one CTA's shared memory; larger graphs go through the two-phase hook

@@ -54,7 +54,7 @@ class cc_options(ctypes.Structure):
         ("flags", ctypes.c_int32),
         ("chunk_arcs", ctypes.c_int32),
         ("tile_vertices", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("sm_limit", ctypes.c_int32),
         ("timeout_ns", ctypes.c_int64),
     ]
 
@@ -92,6 +92,7 @@ SIGNATURES = {
     "cc_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(cc_options)]),
     "cc_set_stream": (ctypes.c_int, [_vp, _vp]),
     "cc_set_options": (ctypes.c_int, [_vp, ctypes.POINTER(cc_options)]),
+    "cc_set_launch_status": (ctypes.c_int, [_vp, _vp]),
     "cc_labels_csr": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
     "cc_labels_coo": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "cc_labels_csr_host": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
@@ -187,11 +188,25 @@ def cc_set_stream(ctx, stream) -> None:
     _check(load().cc_set_stream(ctx, ctypes.c_void_p(_stream_handle(stream))), "cc_set_stream", ctx)
 
 
-def cc_sync(ctx) -> int:
-    """Wait for the context's stream; raise on a pending device error."""
+def cc_sync(ctx, raise_input_errors: bool = True) -> int:
+    """Wait for the context's stream; raise on a pending device error. With
+    raise_input_errors=False a malformed-input report (CC_ERR_OUT_OF_RANGE) is returned instead
+    of raised (a caller that reads per-graph or per-call statuses); fatal errors still raise."""
     st = load().cc_sync(ctx)
+    if st == CC_ERR_OUT_OF_RANGE and not raise_input_errors:
+        return st
     _check(st, "cc_sync", ctx)
     return st
+
+
+def cc_set_launch_status(ctx, device_status=None) -> None:
+    """Per-call input status output: a one-element int32 CUDA tensor (or a device pointer), or
+    None to turn it off. Each following call zeroes it and its kernels set CC_ERR_OUT_OF_RANGE
+    on malformed input."""
+    ptr = None
+    if device_status is not None:
+        ptr = device_status.data_ptr() if hasattr(device_status, "data_ptr") else int(device_status)
+    _check(load().cc_set_launch_status(ctx, ptr), "cc_set_launch_status", ctx)
 
 
 def cc_last_run_info(ctx) -> dict:
@@ -385,8 +400,11 @@ class ConnectedComponents:
     def csr_host(self, row_ptr, col_idx, labels=None):
         return cc_labels_csr_host(self._ctx, row_ptr, col_idx, labels)
 
-    def sync(self):
-        return cc_sync(self._ctx)
+    def sync(self, raise_input_errors: bool = True):
+        return cc_sync(self._ctx, raise_input_errors)
+
+    def set_launch_status(self, device_status=None):
+        cc_set_launch_status(self._ctx, device_status)
 
     def run_info(self):
         return cc_last_run_info(self._ctx)

@@ -21,6 +21,7 @@ struct cc_ctx {
   cc_run_info last{};
   int skip_arrival_block = -1;
   char last_error[256] = {0};
+  int32_t* status_out = nullptr;          // cc_set_launch_status: per-call input status (device)
   unsigned long long* d_phase = nullptr;  // CC_FLAG_PHASE_TIMES timestamps (kPhaseSlots)
   bool phase_valid = false;
   // worklist of the two-phase hierarchical hook
@@ -134,6 +135,13 @@ void resolve_options(cc_options* o) {
   if (o->timeout_ns <= 0) o->timeout_ns = kDefaultTimeoutNs;
 }
 
+// SMs a context's launches may fill: cc_options.sm_limit (a share of the GPU, so that launches of
+// several contexts run side by side), or all of them.
+int usable_sms(const cc_ctx* ctx) {
+  const int lim = ctx->opt.sm_limit;
+  return lim > 0 && lim < ctx->num_sms ? lim : ctx->num_sms;
+}
+
 // Window of the two-phase hook for `want` vertices: a power of two, at least 256, no wider
 // than needed to cover V.
 int window_for(long long V, int want) {
@@ -149,7 +157,7 @@ int window_for(long long V, int want) {
 // CTA count would leave most CTAs idle in the last round).
 int balanced_window(const cc_ctx* ctx, cc::Problem p, int block) {
   p.tile_w = kMaxAutoWindow;
-  const long long ctas = (long long)std::max(1, cc::phase_a_blocks_per_sm(p, block)) * ctx->num_sms;
+  const long long ctas = (long long)std::max(1, cc::phase_a_blocks_per_sm(p, block)) * usable_sms(ctx);
   const long long rounds = std::max<long long>(1, (p.V + ctas * kMaxAutoWindow - 1) / (ctas * kMaxAutoWindow));
   long long w = (p.V + rounds * ctas - 1) / (rounds * ctas);
   w = (w + 255) / 256 * 256;
@@ -209,7 +217,7 @@ bool options_ok(const cc_options* o) {
       (o->tile_vertices < 256 || o->tile_vertices > kMaxTileVertices ||
        (o->tile_vertices & (o->tile_vertices - 1)) != 0))
     return false;
-  if (o->reserved != 0) return false;
+  if (o->sm_limit < 0) return false;
   if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0)) return false;
   if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC | CC_FLAG_PHASE_TIMES)) return false;
   return true;
@@ -220,16 +228,30 @@ cc_status read_and_clear_status(cc_ctx* ctx) {
                                   ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_sync");
-  const int err = ctx->h_status->error;
+  const cc::DevStatus& h = *ctx->h_status;
+  const int err = h.error != 0 ? h.error : h.input_error;
   if (err != 0) {
-    std::snprintf(ctx->last_error, sizeof(ctx->last_error), "device error %d at site %d (info %lld)", err,
-                  ctx->h_status->error_where, ctx->h_status->error_info);
+    if (h.error != 0)
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error), "device error %d at site %d (info %lld)", err,
+                    h.error_where, h.error_info);
+    else
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error), "malformed input (error %d) at site %d (info %lld)",
+                    err, h.input_where, h.input_info);
     e = cudaMemsetAsync(ctx->d_status, 0, sizeof(cc::DevStatus), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_sync clear");
     return (cc_status)err;
   }
   return CC_OK;
+}
+
+// A call with nothing to label: the caller's status output (if any) still reads 0 afterwards.
+cc_status finish_empty_call(cc_ctx* ctx) {
+  if (ctx->status_out) {
+    cudaError_t e = cudaMemsetAsync(ctx->status_out, 0, sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status reset");
+  }
+  return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
 }
 
 // Grows a context-owned device buffer to at least `n` elements of T.
@@ -340,8 +362,16 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   }
 
   info.block = block;
+  // Per-call status: the per-launch fields of the status block (validation's abort flag
+  // included) and the caller's status output start at zero.
+  {
+    cudaError_t e0 = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
+    if (e0 == cudaSuccess && ctx->status_out) e0 = cudaMemsetAsync(ctx->status_out, 0, sizeof(int32_t), ctx->stream);
+    if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "status reset");
+    c.status_out = ctx->status_out;
+  }
   if (o.flags & CC_FLAG_VALIDATE) {
-    cc::LaunchShape vs{(int)std::min<long long>(want, (long long)ctx->num_sms * 8), block};
+    cc::LaunchShape vs{(int)std::min<long long>(want, (long long)usable_sms(ctx) * 8), block};
     cudaError_t e = cc::launch_validate(p, c, vs, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "validate launch");
     info.launches += 1;
@@ -399,7 +429,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     info.block = block;
     if (per_sm <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "persistent occupancy");
     want = std::max<long long>(1, (work + block - 1) / block);
-    const long long cap = (long long)per_sm * ctx->num_sms;
+    const long long cap = (long long)per_sm * usable_sms(ctx);
     long long grid = o.grid_blocks > 0 ? std::min<long long>(o.grid_blocks, cap) : std::min(want, cap);
     cc::LaunchShape s{(int)grid, block};
     if (o.chunk_arcs == 0) {
@@ -408,8 +438,8 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     }
     c.skip_arrival_block = ctx->skip_arrival_block;
     ctx->skip_arrival_block = -1;
-    cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
-    if (e == cudaSuccess && (o.flags & CC_FLAG_PHASE_TIMES)) {
+    cudaError_t e = cudaSuccess;
+    if (o.flags & CC_FLAG_PHASE_TIMES) {
       if (!ctx->d_phase && cudaMalloc(&ctx->d_phase, kPhaseSlots * sizeof(unsigned long long)) != cudaSuccess) {
         ctx->d_phase = nullptr;
         cudaGetLastError();
@@ -432,7 +462,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
       }
       if (per_sm_a <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "phase A occupancy");
       const long long n_units = (p.V + p.tile_w - 1) / p.tile_w;
-      const long long grid_a = std::min<long long>(n_units, (long long)per_sm_a * ctx->num_sms);
+      const long long grid_a = std::min<long long>(n_units, (long long)per_sm_a * usable_sms(ctx));
       e = cc::launch_two_phase(p, c, cc::LaunchShape{(int)grid_a, block_a}, s, ctx->stream);
       info.launches += 2;
     } else if (e == cudaSuccess) {
@@ -444,7 +474,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   } else if (mode == CC_MODE_SOMAN || mode == CC_MODE_SOMAN_MULTIJUMP) {
     if (p.kind != cc::kKindCsr) return CC_ERR_INVALID_ARG;
     const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
-    const long long cap = (long long)per_sm * ctx->num_sms;
+    const long long cap = (long long)per_sm * usable_sms(ctx);
     long long grid = o.grid_blocks > 0 ? o.grid_blocks : std::min(want, cap);
     cc::LaunchShape s{(int)grid, block};
     const cc_status st = run_host_loop(ctx, p, c, s, mode == CC_MODE_SOMAN_MULTIJUMP, &info);
@@ -452,7 +482,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     info.grid_blocks = s.grid;
   } else {
     const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
-    const long long cap = (long long)per_sm * ctx->num_sms;
+    const long long cap = (long long)per_sm * usable_sms(ctx);
     long long grid = o.grid_blocks > 0 ? o.grid_blocks : std::min(want, cap);
     cc::LaunchShape s{(int)grid, block};
     int n = 0;
@@ -536,6 +566,12 @@ cc_status cc_set_stream(cc_ctx* ctx, void* stream) {
   return CC_OK;
 }
 
+cc_status cc_set_launch_status(cc_ctx* ctx, int32_t* device_status) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->status_out = device_status;
+  return CC_OK;
+}
+
 cc_status cc_set_options(cc_ctx* ctx, const cc_options* opt) {
   if (!ctx || !opt || !options_ok(opt)) return CC_ERR_INVALID_ARG;
   ctx->opt = *opt;
@@ -565,7 +601,7 @@ cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const v
   DeviceGuard g(ctx->device);
   if (!g.ok) return CC_ERR_CUDA;
   ctx->last = cc_run_info{};
-  if (n_vertices == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  if (n_vertices == 0) return finish_empty_call(ctx);
   cc::Problem p{};
   p.kind = cc::kKindCsr;
   p.rp = row_ptr;
@@ -590,7 +626,7 @@ cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const 
   DeviceGuard g(ctx->device);
   if (!g.ok) return CC_ERR_CUDA;
   ctx->last = cc_run_info{};
-  if (n_vertices == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  if (n_vertices == 0) return finish_empty_call(ctx);
   cc::Problem p{};
   p.kind = cc::kKindCoo;
   p.src = src;
@@ -621,7 +657,7 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
     per_sm = cc::batched_blocks_per_sm(sym, block, W);
   }
   if (per_sm <= 0) return cuda_fail(ctx, cudaErrorInvalidConfiguration, "batched occupancy");
-  long long grid = (long long)per_sm * ctx->num_sms;
+  long long grid = (long long)per_sm * usable_sms(ctx);
   if (o.grid_blocks > 0) grid = std::min<long long>(grid, o.grid_blocks);
 
   // Scratch: window table, worklist (one pair per vertex, at least 2^20, at most one per arc),
@@ -655,6 +691,8 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   p.sym = sym;
 
   cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
+  if (e == cudaSuccess && ctx->status_out) e = cudaMemsetAsync(ctx->status_out, 0, sizeof(int32_t), ctx->stream);
+  c.status_out = ctx->status_out;
   if (e == cudaSuccess && p.graph_status)
     e = cudaMemsetAsync(p.graph_status, 0, sizeof(int32_t) * n_graphs, ctx->stream);
   if (e == cudaSuccess && (o.flags & CC_FLAG_PHASE_TIMES)) {
@@ -699,7 +737,7 @@ cc_status cc_labels_batched(cc_ctx* ctx, int32_t n_graphs, int64_t total_vertice
   DeviceGuard g(ctx->device);
   if (!g.ok) return CC_ERR_CUDA;
   ctx->last = cc_run_info{};
-  if (n_graphs == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  if (n_graphs == 0) return finish_empty_call(ctx);
   cc::BatchProblem p{};
   p.n_graphs = n_graphs;
   p.v_off = reinterpret_cast<const long long*>(v_off);
@@ -727,7 +765,7 @@ cc_status cc_labels_batched_desc(cc_ctx* ctx, int32_t n_graphs, const cc_graph_d
   DeviceGuard g(ctx->device);
   if (!g.ok) return CC_ERR_CUDA;
   ctx->last = cc_run_info{};
-  if (n_graphs == 0) return (ctx->opt.flags & CC_FLAG_SYNC) ? read_and_clear_status(ctx) : CC_OK;
+  if (n_graphs == 0) return finish_empty_call(ctx);
   static_assert(sizeof(cc_graph_desc) == sizeof(cc::GraphDesc), "descriptor layouts must agree");
   cc::BatchProblem p{};
   p.n_graphs = n_graphs;

@@ -64,7 +64,7 @@ __device__ __forceinline__ long long graph_vertices(const Batch& b, int g, const
                   d.label_off + d.n_vertices <= (long long)b.total_v && d.row_off >= 0 &&
                   d.row_off + d.n_vertices + 1 <= b.row_elems && d.arc_off >= 0 && d.arc_off + d.n_arcs <= b.arc_elems;
   if (!ok) {
-    raise_error(c.st, kErrOutOfRange, kSiteValidate, (long long)g);
+    raise_input_error(c, kSiteValidate, (long long)g);
     if (b.graph_status) b.graph_status[g] = kErrOutOfRange;
     return 0;
   }
@@ -200,7 +200,7 @@ __device__ __forceinline__ void batched_row_heads(const Batch& b, const UnitInfo
     const int u = ui.w0 + i;
     int a0 = ui.rp[u], a1 = ui.rp[u + 1];
     if (!(a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz)) {
-      raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+      raise_input_error(c, kSiteHookArc, (long long)ui.g);
       if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
       a1 = a0;
     }
@@ -212,7 +212,7 @@ __device__ __forceinline__ void batched_row_heads(const Batch& b, const UnitInfo
       const int v = has ? ld_stream(ui.col + a0 + j) : 0;
       const bool in_range = (unsigned)v < (unsigned)ui.vg;
       if (has && !in_range) {
-        raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+        raise_input_error(c, kSiteHookArc, (long long)ui.g);
         if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
       }
       live[j] = has && in_range && v != u;
@@ -243,7 +243,7 @@ __device__ __forceinline__ void batched_rows_outside(const Batch& b, const UnitI
       for (int a = a0; a < a1; ++a) {
         const int v = ld_stream(ui.col + a);
         if ((unsigned)v >= (unsigned)ui.vg) {
-          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
           if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
           continue;
         }
@@ -262,7 +262,7 @@ __device__ __forceinline__ void batched_rows_outside(const Batch& b, const UnitI
         const int v = has ? ld_stream(ui.col + a) : 0;
         const bool in_range = (unsigned)v < (unsigned)ui.vg;
         if (has && !in_range) {
-          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
           if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
         }
         const int uu[1] = {ui.vbase + hu}, vv[1] = {ui.vbase + v};
@@ -280,7 +280,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   __shared__ unsigned long long s_unit;
   __shared__ int s_ovf, s_bad, s_plain;
   __shared__ int s_warp_bad[kMaxBlockB / 32];
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   unsigned epoch = 0;
   const int W = c.tile_w;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +331,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       if (ui.nnz > 0x7fffffffLL) {  // graph too large for int32 row offsets: reported, not hooked
         local = true;
         if (threadIdx.x == 0) {
-          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
           s_bad = 1;
         }
       }
@@ -498,7 +498,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
             hook_csr_range<int, SYM, kHookK>(ui.rp, ui.col, b.labels, ui.vg, t0, t1, c, ui.w0, ui.vbase,
                                              s_warp_bad + warp);
         } else if (lane == 0) {
-          raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)ui.g);
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
           s_warp_bad[warp] = 1;
         }
         __syncwarp();

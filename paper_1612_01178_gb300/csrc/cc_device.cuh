@@ -19,20 +19,25 @@ namespace cc {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Device status block owned by the context. `bar` is zeroed before each
-// persistent launch; `error` is sticky until the host reads and clears it.
+// Device status block owned by the context. The per-launch fields are zeroed before each
+// labelling call; the sticky fields stay set until the host reads and clears them.
 struct DevStatus {
-  // per-launch fields (zeroed before every launch)
+  // per-launch fields (zeroed before every call)
   unsigned int bar;
   unsigned int changed;  // change flag of the host-driven modes (Fig. 1)
   unsigned long long counters[4];  // [0],[1] work counters; [2] worklist cursor; [3] overflowed units
   unsigned long long report[2];    // [0] worklist pairs, [1] worklist segments (hierarchical hook)
-  // sticky error fields (cleared when the host reads them)
-  int error;
+  unsigned int abort;    // validation failed: the launches of this call stop before hooking
+  unsigned int pad;
+  // sticky fields (cleared when the host reads them)
+  int error;             // fatal (a wait ran out, a guard fired): later launches of the context exit early
   int error_where;
   long long error_info;
+  int input_error;       // malformed input found (CC_ERR_OUT_OF_RANGE): reported, later launches run normally
+  int input_where;
+  long long input_info;
 };
-constexpr size_t kPerLaunchStatusBytes = 56;  // bar, changed, counters, report
+constexpr size_t kPerLaunchStatusBytes = 64;  // bar, changed, counters, report, abort, pad
 
 // Where an error was raised (DevStatus::error_where).
 enum ErrorSite : int {
@@ -61,6 +66,7 @@ struct Ctl {
   int ovf_cap = 0;
   int segments_b = 0;                     // segments of the global phase (0 = 2|E'|/|V|)
   int window_mode = 0;                    // batched: kWindowsSampled or kWindowsPlain
+  int* status_out = nullptr;              // optional per-call input status (CC_ERR_OUT_OF_RANGE or left 0)
   unsigned long long* phase_ns = nullptr; // optional per-barrier timestamps (block 0)
   int phase_cap = 0;
   int phase_off = 0;                      // slot of the first barrier's timestamp, minus one
@@ -122,11 +128,29 @@ __device__ __forceinline__ T ld_ro(const T* p) {
   return __ldg(p);
 }
 
+// A fatal device error: the launch stops at its next grid barrier and later launches of the
+// context exit at once until the host has read the error.
 __device__ __forceinline__ void raise_error(DevStatus* st, int code, int where, long long info) {
   if (atomicCAS(&st->error, 0, code) == 0) {
     st->error_where = where;
     st->error_info = info;
   }
+}
+
+// Malformed input (an arc endpoint outside [0, V), offsets inconsistent with n_arcs): the bad
+// arc or row is skipped and reported; the launch and later launches carry on, so in a batch
+// every other graph is still labelled. Also written to the call's status output, if any.
+__device__ __forceinline__ void raise_input_error(const Ctl& c, int where, long long info) {
+  if (atomicCAS(&c.st->input_error, 0, (int)kErrOutOfRange) == 0) {
+    c.st->input_where = where;
+    c.st->input_info = info;
+  }
+  if (c.status_out) *c.status_out = (int)kErrOutOfRange;
+}
+
+// True when this launch must not run: a fatal error is pending or the call's validation failed.
+__device__ __forceinline__ bool launch_blocked(const Ctl& c) {
+  return ld_relaxed(&c.st->error) != 0 || ld_relaxed(reinterpret_cast<const int*>(&c.st->abort)) != 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -147,7 +171,7 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
     const unsigned long long t0 = now_ns();
     for (unsigned spin = 0;; ++spin) {
       if (ld_acquire(&c.st->bar) >= target) break;
-      if (ld_relaxed(&c.st->error) != 0) {
+      if (launch_blocked(c)) {
         go = 0;
         break;
       }
@@ -157,7 +181,7 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
         break;
       }
     }
-    if (go && ld_relaxed(&c.st->error) != 0) go = 0;
+    if (go && launch_blocked(c)) go = 0;
     __threadfence();
     if (c.phase_ns && blockIdx.x == 0 && (int)epoch + c.phase_off < c.phase_cap - 1)
       c.phase_ns[epoch + c.phase_off] = now_ns();
@@ -690,7 +714,7 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         if (valid) {
           const bool in_range = (unsigned)v[j] < (unsigned)V && (unsigned)u[j] < (unsigned)V;
           if (!in_range) {
-            raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a);
+            raise_input_error(c, kSiteHookArc, (long long)a);
             if (bad) *bad = 1;
           }
           live[j] = in_range && !(SYM ? (u[j] >= v[j]) : (u[j] == v[j]));
@@ -781,7 +805,7 @@ __device__ __forceinline__ void hook_row_heads(const OffT* __restrict__ rp, cons
     const int u = (int)x;
     OffT a0 = ld_ro(rp + u), a1 = ld_ro(rp + u + 1);
     if (!(a0 >= 0 && a0 <= a1 && a1 <= nnz)) {
-      raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)u);
+      raise_input_error(c, kSiteHookArc, (long long)u);
       a1 = a0;
     }
     int uu[kSampleArcs], v[kSampleArcs];
@@ -791,7 +815,7 @@ __device__ __forceinline__ void hook_row_heads(const OffT* __restrict__ rp, cons
       const bool has = (long long)a0 + j < (long long)a1;
       v[j] = has ? ld_stream(col + a0 + j) : 0;
       const bool in_range = (unsigned)v[j] < (unsigned)V;
-      if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)a0 + j);
+      if (has && !in_range) raise_input_error(c, kSiteHookArc, (long long)a0 + j);
       live[j] = has && in_range && v[j] != u;
       uu[j] = u;
     }
@@ -849,7 +873,7 @@ __device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, c
       for (long long a = a0; a < a1; ++a) {
         const int v = ld_stream(col + a);
         if ((unsigned)v >= (unsigned)V) {
-          raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+          raise_input_error(c, kSiteHookArc, a);
           continue;
         }
         if (v != u) atomic_hook(pi, u, v, V, c);
@@ -866,7 +890,7 @@ __device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, c
         const bool has = a < h1;
         const int v = has ? ld_stream(col + a) : 0;
         const bool in_range = (unsigned)v < (unsigned)V;
-        if (has && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, a);
+        if (has && !in_range) raise_input_error(c, kSiteHookArc, a);
         const int uu[1] = {hu}, vv[1] = {v};
         const bool live[1] = {has && in_range && v != hu};
         atomic_hook_k<1>(pi, uu, vv, live, V, c);
@@ -919,7 +943,7 @@ __device__ __forceinline__ void load_row_span(const OffT* __restrict__ rp, int w
 template <typename OffT>
 __device__ __forceinline__ void check_span(OffT& x0, OffT& x1, OffT nnz, int u, const Ctl& c) {
   if (!(x0 >= 0 && x0 <= x1 && x1 <= nnz)) {
-    raise_error(c.st, kErrOutOfRange, kSiteHookArc, (long long)u);
+    raise_input_error(c, kSiteHookArc, (long long)u);
     x0 = 0;
     x1 = 0;
   }
@@ -1062,7 +1086,7 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
   sink_flush(sink, c);
   if (sink.flags & kSinkOverflow) *ovf = 1;
   if (sink.flags & kSinkBadArc) {
-    raise_error(c.st, kErrOutOfRange, kSiteWindowRow, (long long)w0 + (sink.flags >> 2) - 1);
+    raise_input_error(c, kSiteWindowRow, (long long)w0 + (sink.flags >> 2) - 1);
     *bad = 1;
   }
   sink.flags = 0;
@@ -1210,7 +1234,7 @@ __device__ __forceinline__ void hook_coo_edges(const int* __restrict__ src, cons
       u[j] = valid ? ld_stream(src + i) : 0;
       v[j] = valid ? ld_stream(dst + i) : 0;
       const bool in_range = (unsigned)u[j] < (unsigned)V && (unsigned)v[j] < (unsigned)V;
-      if (valid && !in_range) raise_error(c.st, kErrOutOfRange, kSiteHookArc, i);
+      if (valid && !in_range) raise_input_error(c, kSiteHookArc, i);
       live[j] = valid && in_range && u[j] != v[j];
     }
     atomic_hook_k<K>(pi, u, v, live, V, c);

@@ -130,5 +130,5 @@ extern "C" cc_status cc_labels_csr_noalloc(int64_t n_vertices, int64_t n_arcs, c
     cudaGetLastError();
     return CC_ERR_CUDA;
   }
-  return (cc_status)result.error;
+  return (cc_status)(result.error != 0 ? result.error : result.input_error);
 }

@@ -33,7 +33,7 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 template <typename OffT, bool SYM>
 __device__ __forceinline__ void csr_persistent_body(const OffT* __restrict__ rp, const int* __restrict__ col,
                                                     int* pi, int V, OffT nnz, int s, const Ctl& c) {
-  if (ld_relaxed(&c.st->error) != 0) return;  // a pending error stops all device work
+  if (launch_blocked(c)) return;  // a pending fatal error or a failed validation stops device work
   unsigned epoch = 0;
   const long long tid = global_tid(), nt = global_threads();
   init_pi(pi, V, tid, nt);
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_csr_filtered(const OffT* __res
                                                                const int* __restrict__ col, int* pi, int V, OffT nnz,
                                                                Ctl c) {
   phase_start(c);
-  if (ld_relaxed(&c.st->error) == 0) {
+  if (!launch_blocked(c)) {
     unsigned epoch = 0;
     const long long tid = global_tid(), nt = global_threads();
     init_pi(pi, V, tid, nt);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_phase_a(const OffT* __restrict
                                                           int* pi, int V, OffT nnz, Ctl c) {
   extern __shared__ __align__(16) unsigned char dyn_smem_a[];
   phase_start(c);
-  if (ld_relaxed(&c.st->error) == 0) tiled_phase_a<OffT, SYM, int>(rp, col, pi, V, nnz, dyn_smem_a, c);
+  if (!launch_blocked(c)) tiled_phase_a<OffT, SYM, int>(rp, col, pi, V, nnz, dyn_smem_a, c);
   if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + 1, now_ns());
 }
 
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_phase_a(const OffT* __restrict
 template <typename OffT, bool SYM>
 __global__ void __launch_bounds__(kMaxBlock, 1) k_phase_b(const OffT* __restrict__ rp, const int* __restrict__ col,
                                                           int* pi, int V, OffT nnz, Ctl c) {
-  if (ld_relaxed(&c.st->error) == 0) {
+  if (!launch_blocked(c)) {
     unsigned epoch = 0;
     const long long tid = global_tid(), nt = global_threads();
     const unsigned long long cur = ld_volatile_u64(&c.st->counters[2]);
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_phase_b(const OffT* __restrict
 
 __device__ __forceinline__ void coo_persistent_body(const int* __restrict__ src, const int* __restrict__ dst,
                                                     int* pi, int V, long long E, int s, const Ctl& c) {
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   unsigned epoch = 0;
   const long long tid = global_tid(), nt = global_threads();
   init_pi(pi, V, tid, nt);
@@ -173,20 +173,20 @@ __global__ void __launch_bounds__(kMaxBlock, 1) k_coo_persistent(const int* __re
 
 __global__ void __launch_bounds__(kMaxBlock) k_init(int* pi, int V, Ctl c) {
   if (global_tid() == 0) c.st->counters[0] = 0ull;
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   init_pi(pi, V, global_tid(), global_threads());
 }
 
 template <typename OffT, bool SYM>
 __global__ void __launch_bounds__(kMaxBlock) k_hook_csr(const OffT* __restrict__ rp, const int* __restrict__ col,
                                                         int* pi, int V, OffT a0, OffT a1, Ctl c) {
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   hook_csr_arcs<OffT, SYM>(rp, col, pi, V, a0, a1, global_tid(), global_threads(), &c.st->counters[0], c);
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_hook_coo(const int* __restrict__ src, const int* __restrict__ dst,
                                                         int* pi, int V, long long e0, long long e1, Ctl c) {
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   hook_coo_edges(src, dst, pi, V, e0, e1, global_tid(), global_threads(), c);
 }
 
@@ -194,18 +194,18 @@ template <typename OffT, bool SYM>
 __global__ void __launch_bounds__(kMaxBlock) k_hook_csr_nonatomic(const OffT* __restrict__ rp,
                                                                   const int* __restrict__ col, int* pi, int V, OffT nnz,
                                                                   Ctl c) {
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   hook_csr_arcs<OffT, SYM, kHookNonAtomic>(rp, col, pi, V, (OffT)0, nnz, global_tid(), global_threads(), nullptr, c);
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_jump_single(int* pi, int V, Ctl c) {
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   single_jump(pi, V, global_tid(), global_threads(), c);
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_jump(int* pi, int V, Ctl c) {
   if (global_tid() == 0) c.st->counters[0] = 0ull;
-  if (ld_relaxed(&c.st->error) != 0) return;
+  if (launch_blocked(c)) return;
   multi_jump(pi, V, global_tid(), global_threads(), c);
 }
 
@@ -247,23 +247,29 @@ __global__ void __launch_bounds__(256) k_sample_locality(const OffT* __restrict_
 }
 
 // ----- validation (CC_FLAG_VALIDATE) -----
+// A failed check is reported as an input error and stops the rest of the call (DevStatus::abort),
+// so the hooks never follow offsets found bad.
+__device__ __forceinline__ void fail_validation(const Ctl& c, long long info) {
+  raise_input_error(c, kSiteValidate, info);
+  c.st->abort = 1u;
+}
 
 template <typename OffT>
 __global__ void __launch_bounds__(kMaxBlock) k_validate_csr(const OffT* __restrict__ rp, const int* __restrict__ col,
                                                             int V, OffT nnz, Ctl c) {
   const long long tid = global_tid(), nt = global_threads();
-  if (tid == 0 && (rp[0] != 0 || rp[V] != nnz)) raise_error(c.st, kErrOutOfRange, kSiteValidate, -1);
+  if (tid == 0 && (rp[0] != 0 || rp[V] != nnz)) fail_validation(c, -1);
   for (long long v = tid; v < V; v += nt)
-    if (rp[v + 1] < rp[v]) raise_error(c.st, kErrOutOfRange, kSiteValidate, v);
+    if (rp[v + 1] < rp[v]) fail_validation(c, v);
   for (long long a = tid; a < (long long)nnz; a += nt)
-    if ((unsigned)col[a] >= (unsigned)V) raise_error(c.st, kErrOutOfRange, kSiteValidate, a);
+    if ((unsigned)col[a] >= (unsigned)V) fail_validation(c, a);
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_validate_coo(const int* __restrict__ src, const int* __restrict__ dst,
                                                             int V, long long E, Ctl c) {
   for (long long i = global_tid(); i < E; i += global_threads())
     if ((unsigned)src[i] >= (unsigned)V || (unsigned)dst[i] >= (unsigned)V)
-      raise_error(c.st, kErrOutOfRange, kSiteValidate, i);
+      fail_validation(c, i);
 }
 
 // ----- host helpers -----

@@ -140,13 +140,82 @@ def test_per_graph_status(dev):
             cc.sync()
         assert ei.value.status == ccapi.CC_ERR_OUT_OF_RANGE
         assert list(st.cpu().numpy()) == [0, ccapi.CC_ERR_OUT_OF_RANGE, 0]
-        # graphs without errors are still labelled correctly... but work stops at the first barrier
-        # after an error, so only the per-graph status is asserted; a clean batch then succeeds:
+        # a malformed graph is reported but does not stop the launch: the other graphs are labelled
+        got = out.cpu().numpy()
+        for g in (0, 2):
+            v0, v1 = int(b.v_off[g]), int(b.v_off[g + 1])
+            grp, gcol = b.graph(g)
+            assert np.array_equal(got[v0:v1], oracle.labels_uf_csr(grp, gcol)[0]), f"graph {g}"
         b2 = gen.batch_from_graphs([graphs[0], graphs[2]])
         v_off, a_off, rp, colt = to_dev(dev, b2)
         out = cc.batched(v_off, a_off, rp, colt)
         cc.sync()
         assert_batch(out.cpu().numpy(), b2)
+
+
+@pytest.mark.parametrize("n_good", [3, 600])
+def test_bad_graphs_do_not_stop_the_batch(dev, n_good):
+    """Malformed graphs (an endpoint outside [0, V_g), offsets past the graph's arcs) spread over a
+    batch of windows of every kind: each is reported in graph_status and every other graph still
+    equals the oracle, and the next call on the same context is unaffected."""
+    rng = np.random.default_rng(40 + n_good)
+    graphs, bad = [], set()
+    for i in range(n_good):
+        kind = i % 3
+        if kind == 0:
+            g = gen.er_csr(int(rng.integers(50, 3000)), int(rng.integers(50, 9000)), seed=1000 + i)
+        elif kind == 1:
+            g = gen.grid_csr(int(rng.integers(10, 250)), 0.9, seed=1000 + i)
+        else:
+            g = gen.rmat_csr(int(rng.integers(8, 16)), 8, seed=1000 + i)
+        graphs.append(g)
+    graphs.append(gen.grid_csr(700, 0.9, seed=7))   # several windows (phase A)
+    graphs.append(gen.rmat_csr(17, 8, seed=8))      # several windows without locality
+    for j in sorted(rng.choice(len(graphs), size=min(5, len(graphs)), replace=False).tolist()):
+        g = graphs[j]
+        if g.nnz == 0:
+            continue
+        col = g.col.copy()
+        rp = g.row_ptr.copy()
+        if j % 2 == 0:  # the first arc of a row: every hook variant reads it
+            rows = np.flatnonzero(np.diff(g.row_ptr) > 0)
+            col[int(g.row_ptr[int(rng.choice(rows))])] = g.n_vertices + int(rng.integers(0, 50))
+        else:
+            rp[g.n_vertices // 2 + 1:] = rp[g.n_vertices // 2 + 1:] + 3  # offsets past the arc range
+            rp[-1] = g.nnz
+        graphs[j] = gen.CSR(g.n_vertices, rp, col, g.n_edges, "bad")
+        bad.add(j)
+    b = gen.batch_from_graphs(graphs)
+    good_want = {}
+    for g in range(b.n_graphs):
+        if g not in bad:
+            grp, gcol = b.graph(g)
+            good_want[g] = oracle.labels_uf_csr(grp, gcol)[0]
+    with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYMMETRIC) as cc:
+        v_off, a_off, rp, colt = to_dev(dev, b)
+        st = torch.full((b.n_graphs,), -7, dtype=torch.int32, device=dev)
+        out = cc.batched(v_off, a_off, rp, colt, graph_status=st)
+        assert cc.sync(raise_input_errors=False) == ccapi.CC_ERR_OUT_OF_RANGE
+        status = st.cpu().numpy()
+        got = out.cpu().numpy()
+        for g in range(b.n_graphs):
+            if g in bad:
+                continue
+            assert status[g] == 0, f"graph {g} flagged"
+            v0, v1 = int(b.v_off[g]), int(b.v_off[g + 1])
+            assert np.array_equal(got[v0:v1], good_want[g]), f"graph {g} ({b.kinds[g]}) differs"
+        # bad offsets that stay inside the graph's own arc range may go unnoticed (its labels are
+        # unspecified); an endpoint out of range in the first arc of a row is always seen
+        for j in bad:
+            if j % 2 == 0:
+                assert status[j] == ccapi.CC_ERR_OUT_OF_RANGE, f"bad graph {j} not flagged"
+        # the next call on the same context: the good graphs alone, nothing left over
+        good = [graphs[g] for g in range(len(graphs)) if g not in bad]
+        b2 = gen.batch_from_graphs(good)
+        v_off, a_off, rp, colt = to_dev(dev, b2)
+        out2 = cc.batched(v_off, a_off, rp, colt)
+        assert cc.sync() == ccapi.CC_OK
+        assert_batch(out2.cpu().numpy(), b2, what="after a batch with bad graphs")
 
 
 def test_batched_argument_errors(dev):

@@ -144,6 +144,9 @@ typedef struct cc_options {
                           co-resident blocks (a share of the GPU, so that the launches of several
                           contexts on different streams run side by side); 0 = all SMs */
   int64_t timeout_ns;  /* limit of every device-side wait; 0 = 2 s */
+  int64_t stream_arcs; /* cc_labels_csr_host only: > 0 = leave the arcs in host memory and stream
+                          them in segments of this many arcs (see cc_labels_csr_host); 0 = stream
+                          only when the graph does not fit in free device memory */
 } cc_options;
 
 /* Fills *opt with the defaults (all zero fields resolved as documented above). */
@@ -239,7 +242,19 @@ cc_status cc_labels_batched_desc(cc_ctx* ctx, int32_t n_graphs, const cc_graph_d
    (pinned memory gives full copy bandwidth) into context-owned device buffers,
    runs the method, copies the labels back into the host array `labels`, and
    returns after the copy completes (always synchronous). The device buffers
-   grow to the largest graph seen and are freed by cc_destroy. */
+   grow to the largest graph seen and are freed by cc_destroy.
+   Graphs larger than device memory (Section III-B: the segments bound the
+   working set to the |V|-sized parent array): when cc_options.stream_arcs > 0,
+   or when row_ptr + col_idx + labels do not fit in free device memory, the arcs
+   stay in host memory. row_ptr and the labels (pi) are copied to / kept on the
+   device, and Fig. 4 runs with s = ceil(n_arcs / seg) contiguous segments of
+   seg arcs (stream_arcs, or two buffers sized from the free memory): segment i
+   is copied in on a copy stream while segment i - 1 is Atomic-Hooked (plain
+   hook), and a Multi-Jump follows every segment. The device then holds only
+   row_ptr, labels and two segment buffers. CC_FLAG_VALIDATE does not apply
+   (endpoints are range-checked while hooking); cc_last_run_info reports
+   streamed_segments. Returns CC_ERR_OOM if row_ptr and labels themselves do not
+   fit. */
 cc_status cc_labels_csr_host(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
                              cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels);
 
@@ -258,6 +273,8 @@ typedef struct cc_run_info {
   int64_t worklist_capacity; /* pairs the worklist could hold (hierarchical hook) */
   int32_t host_round_trips;  /* device-to-host flag reads that decided convergence (Soman modes) */
   int32_t hook_rounds;       /* Hook rounds of the host loop (Soman modes) */
+  int32_t streamed_segments; /* cc_labels_csr_host: arc segments streamed from host memory (0 = none) */
+  int32_t reserved;
 } cc_run_info;
 
 /* Worklist of the last hierarchical-hook launch: waits for the context's stream, then

@@ -56,6 +56,7 @@ class cc_options(ctypes.Structure):
         ("tile_vertices", ctypes.c_int32),
         ("sm_limit", ctypes.c_int32),
         ("timeout_ns", ctypes.c_int64),
+        ("stream_arcs", ctypes.c_int64),
     ]
 
 
@@ -70,6 +71,8 @@ class cc_run_info(ctypes.Structure):
         ("worklist_capacity", ctypes.c_int64),
         ("host_round_trips", ctypes.c_int32),
         ("hook_rounds", ctypes.c_int32),
+        ("streamed_segments", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

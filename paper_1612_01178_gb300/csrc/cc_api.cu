@@ -50,6 +50,12 @@ struct cc_ctx {
   size_t d_col_bytes = 0;
   int32_t* d_labels = nullptr;
   size_t d_labels_bytes = 0;
+  // streamed arcs of cc_labels_csr_host (graphs whose arcs stay in host memory)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t seg_copied[2] = {nullptr, nullptr};
+  cudaEvent_t seg_used[2] = {nullptr, nullptr};
+  int32_t* d_seg[2] = {nullptr, nullptr};
+  size_t d_seg_arcs = 0;
 };
 
 namespace cc {
@@ -217,7 +223,7 @@ bool options_ok(const cc_options* o) {
       (o->tile_vertices < 256 || o->tile_vertices > kMaxTileVertices ||
        (o->tile_vertices & (o->tile_vertices - 1)) != 0))
     return false;
-  if (o->sm_limit < 0) return false;
+  if (o->sm_limit < 0 || o->stream_arcs < 0) return false;
   if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0)) return false;
   if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC | CC_FLAG_PHASE_TIMES)) return false;
   return true;
@@ -795,6 +801,126 @@ static cc_status grow(cc_ctx* ctx, void** buf, size_t* have, size_t need) {
   return CC_OK;
 }
 
+// Arcs per streamed segment for cc_labels_csr_host: cc_options.stream_arcs if set, else 0 when
+// the whole graph fits on the device next to a safety margin, else two segment buffers sized
+// from the free memory left after row_ptr and labels (-1 if not even those fit).
+static long long stream_segment_arcs(cc_ctx* ctx, size_t rp_bytes, size_t col_bytes, size_t lab_bytes) {
+  if (ctx->opt.stream_arcs > 0) return ctx->opt.stream_arcs;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t avail = free_b + ctx->d_rp_bytes + ctx->d_col_bytes + ctx->d_labels_bytes +
+                       2 * ctx->d_seg_arcs * sizeof(int32_t);  // buffers this call may reuse
+  const size_t margin = (size_t)1 << 30;
+  if (rp_bytes + col_bytes + lab_bytes + margin <= avail) return 0;
+  const size_t min_seg_bytes = (size_t)1 << 22;
+  if (rp_bytes + lab_bytes + margin + 2 * min_seg_bytes > avail) return -1;
+  const size_t seg_bytes = std::min<size_t>((avail - rp_bytes - lab_bytes - margin) / 2, (size_t)1 << 30);
+  return (long long)(seg_bytes / sizeof(int32_t));
+}
+
+// Fig. 4 with the arcs left in host memory: row_ptr and labels (pi) live on the device, and the
+// s = ceil(n_arcs / seg) segments of the arc array are copied in one after the other on a copy
+// stream, into two device buffers used in turn. Segment i is Atomic-Hooked (plain hook) as soon
+// as it has landed, while segment i + 1 is copied; a Multi-Jump follows every segment. The
+// device holds 4 (V + 1) or 8 (V + 1) + 4 V + 8 seg bytes, whatever n_arcs is.
+static cc_status run_streamed(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
+                              cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels, long long seg) {
+  const cc_options& o = ctx->opt;
+  const size_t rp_bytes = (size_t)(n_vertices + 1) * (size_t)row_ptr_type;
+  const size_t lab_bytes = (size_t)n_vertices * sizeof(int32_t);
+  // the resident arc buffer of the non-streamed path is not needed here
+  if (ctx->d_col) {
+    cudaFree(ctx->d_col);
+    ctx->d_col = nullptr;
+    ctx->d_col_bytes = 0;
+  }
+  cc_status st = grow(ctx, &ctx->d_rp, &ctx->d_rp_bytes, std::max<size_t>(rp_bytes, 16));
+  if (st == CC_OK) st = grow(ctx, (void**)&ctx->d_labels, &ctx->d_labels_bytes, std::max<size_t>(lab_bytes, 16));
+  if (st != CC_OK) return st;
+  if (ctx->d_seg_arcs < (size_t)seg) {
+    for (int b = 0; b < 2; ++b) {
+      if (ctx->d_seg[b]) cudaFree(ctx->d_seg[b]);
+      ctx->d_seg[b] = nullptr;
+    }
+    ctx->d_seg_arcs = 0;
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&ctx->d_seg[b], (size_t)seg * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        std::snprintf(ctx->last_error, sizeof(ctx->last_error), "segment buffer of %lld arcs failed", seg);
+        return CC_ERR_OOM;
+      }
+    }
+    ctx->d_seg_arcs = (size_t)seg;
+  }
+  if (!ctx->copy_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->copy_stream = nullptr;
+      return cuda_fail(ctx, cudaErrorUnknown, "copy stream");
+    }
+    for (int b = 0; b < 2; ++b) {
+      if (cudaEventCreateWithFlags(&ctx->seg_copied[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->seg_used[b], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "segment events");
+    }
+  }
+  cudaStream_t s = ctx->stream;
+  cc::Problem p{};
+  p.kind = cc::kKindCsr;
+  p.rp = ctx->d_rp;
+  p.rp64 = row_ptr_type == CC_INDEX_I64;
+  p.col = nullptr;  // not resident
+  p.pi = ctx->d_labels;
+  p.V = (int)n_vertices;
+  p.m = n_arcs;
+  p.sym = (o.flags & CC_FLAG_SYMMETRIC) != 0;
+  const long long n_seg = (n_arcs + seg - 1) / seg;
+  p.segments = (int)std::min<long long>(n_seg, INT32_MAX);
+  cc::Ctl c;
+  c.st = ctx->d_status;
+  c.timeout_ns = o.timeout_ns;
+  c.status_out = ctx->status_out;
+  const int block = o.block > 0 ? o.block : kPlainBlock;
+  const int per_sm = std::max(1, cc::stage_blocks_per_sm(p, block));
+  const long long work = std::max<long long>(p.V, std::min<long long>(n_arcs, seg) / 4);
+  const long long grid = std::max<long long>(1, std::min<long long>((work + block - 1) / block,
+                                                                    (long long)per_sm * usable_sms(ctx)));
+  const cc::LaunchShape shape{(int)grid, block};
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, s);
+  if (e == cudaSuccess && ctx->status_out) e = cudaMemsetAsync(ctx->status_out, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_rp, row_ptr, rp_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cc::launch_init_only(p, c, shape, s);
+  cc_run_info info{};
+  info.mode = CC_MODE_MULTI_LAUNCH;
+  info.segments = p.segments;
+  info.grid_blocks = (int)grid;
+  info.block = block;
+  info.launches = 1;
+  info.streamed_segments = p.segments;
+  for (long long i = 0; i < n_seg && e == cudaSuccess; ++i) {
+    const int b = (int)(i & 1);
+    const long long a0 = i * seg, a1 = std::min<long long>(n_arcs, a0 + seg);
+    if (i >= 2) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->seg_used[b], 0);  // buffer free again
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->d_seg[b], col_idx + a0, (size_t)(a1 - a0) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                          ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_copied[b], ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->seg_copied[b], 0);
+    c.chunk_arcs = o.chunk_arcs != 0 ? o.chunk_arcs : cc::auto_chunk_arcs(a1 - a0, grid * (block / 32));
+    if (e == cudaSuccess) e = cc::launch_hook_segment(p, ctx->d_seg[b], a0, a1, c, shape, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_used[b], s);
+    if (e == cudaSuccess) e = cc::launch_jump_multi(p, c, shape, s);  // Multi-Jump after every segment
+    info.launches += 2;
+  }
+  if (e == cudaSuccess && lab_bytes) e = cudaMemcpyAsync(labels, ctx->d_labels, lab_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "streamed labelling");
+  ctx->last = info;
+  return read_and_clear_status(ctx);
+}
+
 cc_status cc_labels_csr_host(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
                              cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels) {
   if (!ctx) return CC_ERR_INVALID_ARG;
@@ -807,6 +933,17 @@ cc_status cc_labels_csr_host(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, co
   const size_t rp_bytes = (size_t)(n_vertices + 1) * (size_t)row_ptr_type;
   const size_t col_bytes = (size_t)n_arcs * sizeof(int32_t);
   const size_t lab_bytes = (size_t)n_vertices * sizeof(int32_t);
+  if (n_vertices > 0 && n_arcs > 0) {
+    const long long seg = stream_segment_arcs(ctx, rp_bytes, col_bytes, lab_bytes);
+    if (seg < 0) {
+      std::snprintf(ctx->last_error, sizeof(ctx->last_error), "row_ptr and labels do not fit on the device");
+      return CC_ERR_OOM;
+    }
+    if (seg > 0 && seg < n_arcs) {
+      ctx->last = cc_run_info{};
+      return run_streamed(ctx, n_vertices, n_arcs, row_ptr, row_ptr_type, col_idx, labels, seg);
+    }
+  }
   cc_status st = grow(ctx, &ctx->d_rp, &ctx->d_rp_bytes, std::max<size_t>(rp_bytes, 16));
   if (st == CC_OK) st = grow(ctx, (void**)&ctx->d_col, &ctx->d_col_bytes, std::max<size_t>(col_bytes, 16));
   if (st == CC_OK) st = grow(ctx, (void**)&ctx->d_labels, &ctx->d_labels_bytes, std::max<size_t>(lab_bytes, 16));
@@ -898,6 +1035,15 @@ void cc_destroy(cc_ctx* ctx) {
     if (ctx->d_rp) cudaFree(ctx->d_rp);
     if (ctx->d_col) cudaFree(ctx->d_col);
     if (ctx->d_labels) cudaFree(ctx->d_labels);
+    for (int b = 0; b < 2; ++b) {
+      if (ctx->d_seg[b]) cudaFree(ctx->d_seg[b]);
+      if (ctx->seg_copied[b]) cudaEventDestroy(ctx->seg_copied[b]);
+      if (ctx->seg_used[b]) cudaEventDestroy(ctx->seg_used[b]);
+    }
+    if (ctx->copy_stream) {
+      cudaStreamSynchronize(ctx->copy_stream);
+      cudaStreamDestroy(ctx->copy_stream);
+    }
     if (ctx->d_phase) cudaFree(ctx->d_phase);
     if (ctx->d_wl) cudaFree(ctx->d_wl);
     if (ctx->d_ovf) cudaFree(ctx->d_ovf);

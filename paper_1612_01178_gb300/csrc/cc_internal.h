@@ -108,6 +108,12 @@ cudaError_t launch_hook_nonatomic(const Problem& p, const Ctl& c, LaunchShape s,
 cudaError_t launch_jump_single(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 cudaError_t launch_jump_multi(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 
+// Atomic-Hook of the arcs [a0, a1) of a CSR graph whose arcs are not resident: col_seg is a
+// device buffer holding exactly those arcs (one segment of Fig. 4 streamed in from the host).
+// p.rp and p.pi are on the device. Work counter 0 must be zero (k_init / k_jump reset it).
+cudaError_t launch_hook_segment(const Problem& p, const int* col_seg, long long a0, long long a1, const Ctl& c,
+                                LaunchShape s, cudaStream_t stream);
+
 // Device checks of CSR offsets and endpoints (CC_FLAG_VALIDATE).
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 

@@ -445,6 +445,24 @@ cudaError_t launch_sample_locality(const Problem& p, int W, unsigned long long* 
                        W, out);
 }
 
+cudaError_t launch_hook_segment(const Problem& p, const int* col_seg, long long a0, long long a1, const Ctl& c,
+                                LaunchShape s, cudaStream_t stream) {
+  // col_seg holds the arcs [a0, a1); the kernel indexes arcs by their position in the whole arc
+  // array, so it gets the address col_seg would have if the whole array were resident (only
+  // positions in [a0, a1) are ever read through it).
+  const int* col = reinterpret_cast<const int*>(reinterpret_cast<uintptr_t>(col_seg) - (uintptr_t)a0 * sizeof(int));
+  if (p.rp64) {
+    const long long* rp = static_cast<const long long*>(p.rp);
+    return with_csr_hook<long long>(p, [&](auto k) {
+      return launch_kernel(k, s, 0, false, stream, rp, col, p.pi, p.V, a0, a1, c);
+    });
+  }
+  const int* rp = static_cast<const int*>(p.rp);
+  return with_csr_hook<int>(p, [&](auto k) {
+    return launch_kernel(k, s, 0, false, stream, rp, col, p.pi, p.V, (int)a0, (int)a1, c);
+  });
+}
+
 cudaError_t launch_init_only(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream) {
   return launch_kernel(k_init, s, 0, false, stream, p.pi, p.V, c);
 }

@@ -89,3 +89,25 @@ def test_binding_constants_match_the_header():
     assert {"CC_OK", "CC_FLAG_SYMMETRIC", "CC_MODE_AUTO", "CC_MODE_FILTERED", "CC_INDEX_I64"} <= set(header)
     binding = {k: v for k, v in vars(cc).items() if k.startswith("CC_") and isinstance(v, int)}
     assert binding == header, (sorted(set(binding.items()) ^ set(header.items())))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of cc_options and cc_run_info have the C structs' size and field offsets."""
+    import ctypes
+    from paper_1612_01178_gb300 import cc
+    src = tmp_path / "sizes.c"
+    fields = {"cc_options": [f for f, _ in cc.cc_options._fields_], "cc_run_info": [f for f, _ in cc.cc_run_info._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cc.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("  return 0; }")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, cls in (("cc_options", cc.cc_options), ("cc_run_info", cc.cc_run_info)):
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)

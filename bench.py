@@ -342,8 +342,6 @@ def run_batched(args, rank, world, local_rank):
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream(device=dev)
     flags = ccl.CC_FLAG_SYMMETRIC
-    cc = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, tile_vertices=args.tile,
-                                 segments=args.segments)
     with torch.cuda.stream(stream):
         v_off = torch.from_numpy(b.v_off).to(dev)
         a_off = torch.from_numpy(b.a_off).to(dev)
@@ -352,6 +350,17 @@ def run_batched(args, rank, world, local_rank):
         labels = torch.empty(b.total_vertices, dtype=torch.int32, device=dev)
         flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream.synchronize()
+    tuner, tuned = None, None
+    if args.tune:
+        # the autotuner in the loop: search (starting from the cached best of this batch's bucket),
+        # then the timed context takes the tuned options from the cache
+        from paper_1612_01178_gb300.tune import Tuner
+        tuner = Tuner(args.tune_cache)
+        t_tune = time.perf_counter()
+        best = tuner.tune_batched(v_off, a_off, rp, col, flags=flags, reps=2)
+        tuned = {"options": best, "cache": args.tune_cache, "search_s": round(time.perf_counter() - t_tune, 1)}
+    cc = ccl.ConnectedComponents(local_rank, stream=stream, flags=flags, tile_vertices=args.tile,
+                                 segments=args.segments, tuner=tuner)
     cc.batched(v_off, a_off, rp, col, labels)
     cc.sync()
     got = labels.cpu().numpy()
@@ -485,6 +494,7 @@ def run_batched(args, rank, world, local_rank):
                    "total_arcs": b.total_arcs, "kinds": kinds, "seed": 1, "flags": "CC_FLAG_SYMMETRIC",
                    "window": info["tile_vertices"], "block": info["block"], "grid_blocks": info["grid_blocks"],
                    "worklist": {"pairs": wl[0], "segments": wl[1]},
+                   "tuned": dict(tuned, source=cc.last_options_source) if tuned else None,
                    "l2": "inputs larger than L2; 256 MiB flush between steps",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "generation_s": round(gen_s, 1)},
@@ -969,6 +979,9 @@ def main(argv=None):
     ap.add_argument("--tile", type=int, default=0, help="hook window: 0 = automatic, -1 = plain hook")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="batched: autotune the launch options first and run with them")
+    ap.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "gb300_cc_tune.json"),
+                    help="JSON cache of tuned options per size bucket")
     args = ap.parse_args(argv)
     if args.impl == "ours":
         args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps

@@ -110,7 +110,15 @@ typedef enum cc_mode {
      the sample, the second subset is every arc, hooked as in CC_MODE_PERSISTENT. `segments`,
      `tile_vertices` do not apply. Arcs that are never read are not range-checked: an endpoint
      outside [0, V) in a skipped row goes unreported (CC_FLAG_VALIDATE checks every arc first). */
-  CC_MODE_FILTERED = 5
+  CC_MODE_FILTERED = 5,
+  /* Small graphs, CSR only: one launch of one thread-block cluster (8 CTAs, or 16 where the GPU
+     allows it) holding pi in the CTAs' distributed shared memory, so root walks and hooks are
+     shared-memory accesses and the phases are separated by the cluster barrier. With
+     CC_FLAG_SYMMETRIC it runs the sampled-and-filtered hook, else every arc in one segment.
+     At most 16 x 32768 vertices (8 x 32768 where clusters of 16 are not available), else
+     CC_ERR_INVALID_ARG. CC_MODE_AUTO picks it only up to cluster_max_vertices vertices (off by
+     default; an autotuner knob). */
+  CC_MODE_CLUSTER = 6
 } cc_mode;
 
 typedef struct cc_options {
@@ -147,6 +155,15 @@ typedef struct cc_options {
   int64_t stream_arcs; /* cc_labels_csr_host only: > 0 = leave the arcs in host memory and stream
                           them in segments of this many arcs (see cc_labels_csr_host); 0 = stream
                           only when the graph does not fit in free device memory */
+  /* Knobs of the automatic choices, for an autotuner (0 = the default in brackets): */
+  int32_t hook_k;      /* arcs per lane per step of the plain CSR hook: 1, 2 or 4 [1] */
+  int32_t auto_min_vertices;    /* below this many vertices CC_MODE_AUTO keeps the plain hook [2^17] */
+  int32_t auto_local_permille;  /* sampled arcs inside one window, per mille, for the two-phase hook [500] */
+  int32_t auto_lowdeg_permille; /* sampled rows below a quarter of the mean degree, per mille, for the
+                                   sampled-and-filtered hook [250] */
+  int32_t cluster_max_vertices; /* CC_MODE_AUTO runs the cluster kernel up to this many vertices (and
+                                   2^23 arcs per 2^18 vertices) [0 = never] */
+  int32_t reserved;    /* must be 0 */
 } cc_options;
 
 /* Fills *opt with the defaults (all zero fields resolved as documented above). */
@@ -181,6 +198,17 @@ cc_status cc_set_launch_status(cc_ctx* ctx, int32_t* device_status);
  * (Fig. 4: "s distinct subsets of E"). */
 cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const void* row_ptr,
                         cc_index_type row_ptr_type, const int32_t* col_idx, int32_t* labels);
+
+/* Connected components of a CSR graph with 64-bit vertex IDs, for graphs of more than 2^31 - 1
+ * vertices (Section III-B: the method's working set is the |V|-sized parent array, so the vertex
+ * count is bounded by device memory, 8 bytes per vertex here, not by 32-bit IDs).
+ *   row_ptr     device int64 [V + 1];  col_idx  device int64 [n_arcs], values in [0, V);
+ *   labels      device int64 [V], caller-owned output (also the work array pi).
+ * Runs Fig. 4 with one segment as three launches (init, Atomic-Hook of every arc, Multi-Jump).
+ * CC_FLAG_SYMMETRIC and CC_FLAG_SYNC apply as for cc_labels_csr; the other options do not.
+ * Labels are the minimum vertex ID of each component, as for cc_labels_csr. */
+cc_status cc_labels_csr64(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const int64_t* row_ptr,
+                          const int64_t* col_idx, int64_t* labels);
 
 /* Connected components of an edge list (COO): edge i joins src[i] and dst[i].
  *   src, dst    device int32 [n_edges], values in [0, V); each edge is undirected

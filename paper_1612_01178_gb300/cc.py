@@ -40,6 +40,7 @@ CC_MODE_MULTI_LAUNCH = 2
 CC_MODE_SOMAN = 3
 CC_MODE_SOMAN_MULTIJUMP = 4
 CC_MODE_FILTERED = 5
+CC_MODE_CLUSTER = 6
 
 CC_INDEX_I32 = 4
 CC_INDEX_I64 = 8
@@ -57,6 +58,12 @@ class cc_options(ctypes.Structure):
         ("sm_limit", ctypes.c_int32),
         ("timeout_ns", ctypes.c_int64),
         ("stream_arcs", ctypes.c_int64),
+        ("hook_k", ctypes.c_int32),
+        ("auto_min_vertices", ctypes.c_int32),
+        ("auto_local_permille", ctypes.c_int32),
+        ("auto_lowdeg_permille", ctypes.c_int32),
+        ("cluster_max_vertices", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -98,6 +105,7 @@ SIGNATURES = {
     "cc_set_launch_status": (ctypes.c_int, [_vp, _vp]),
     "cc_labels_csr": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
     "cc_labels_coo": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
+    "cc_labels_csr64": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _vp]),
     "cc_labels_csr_host": (ctypes.c_int, [_vp, _i64, _i64, _vp, ctypes.c_int, _vp, _vp]),
     "cc_labels_batched": (ctypes.c_int, [_vp, _i32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "cc_labels_batched_desc": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
@@ -270,6 +278,26 @@ def cc_labels_csr(ctx, row_ptr, col_idx, labels=None):
     return labels
 
 
+def cc_labels_csr64(ctx, row_ptr, col_idx, labels=None):
+    """Min-ID labels of a CSR graph with 64-bit vertex IDs (int64 CUDA tensors row_ptr, col_idx;
+    int64 labels), for graphs of more than 2^31 - 1 vertices."""
+    import torch
+    _dev_tensor(row_ptr, torch.int64, "row_ptr")
+    _dev_tensor(col_idx, torch.int64, "col_idx")
+    V = row_ptr.numel() - 1
+    if V < 0:
+        raise ValueError("row_ptr must hold V+1 offsets")
+    if labels is None:
+        labels = torch.empty(V, dtype=torch.int64, device=row_ptr.device)
+    _dev_tensor(labels, torch.int64, "labels")
+    if labels.numel() != V:
+        raise ValueError("labels must hold V entries")
+    st = load().cc_labels_csr64(ctx, V, col_idx.numel(), row_ptr.data_ptr(),
+                                col_idx.data_ptr() if col_idx.numel() else None, labels.data_ptr() if V else None)
+    _check(st, "cc_labels_csr64", ctx)
+    return labels
+
+
 def cc_labels_coo(ctx, n_vertices: int, src, dst, labels=None):
     """Min-ID component labels of an undirected edge list (int32 CUDA tensors src, dst)."""
     import torch
@@ -374,10 +402,28 @@ class ConnectedComponents:
     >>> labels = cc.csr(row_ptr, col_idx); cc.sync()
     """
 
-    def __init__(self, device: int = 0, stream=None, **options):
+    def __init__(self, device: int = 0, stream=None, tuner=None, **options):
+        """`tuner` (a tune.Tuner) makes every call look up the tuned options of its graph's size
+        bucket and run with them (the explicit `options` are the fallback for buckets without a
+        tuned entry); `last_options_source` then says which applied."""
         self.device = device
+        self.base_options = dict(options)
         self.options = default_options(**options)
+        self.tuner = tuner
+        self.last_options_source = "explicit"
+        self._applied = dict(options)
         self._ctx = cc_create(device, stream, self.options)
+
+    def _apply_tuned(self, tuned):
+        want = dict(self.base_options)
+        if tuned:
+            want.update(tuned)
+            want["flags"] = self.base_options.get("flags", 0)  # the caller's flags describe the input
+        self.last_options_source = "tuner cache" if tuned else "explicit"
+        if want != self._applied:
+            self.options = default_options(**want)
+            cc_set_options(self._ctx, self.options)
+            self._applied = want
 
     @property
     def handle(self):
@@ -387,17 +433,27 @@ class ConnectedComponents:
         for k, v in options.items():
             setattr(self.options, k, int(v))
         cc_set_options(self._ctx, self.options)
+        self.base_options.update(options)
+        self._applied.update(options)
 
     def set_stream(self, stream):
         cc_set_stream(self._ctx, stream)
 
     def csr(self, row_ptr, col_idx, labels=None):
+        if self.tuner is not None:
+            self._apply_tuned(self.tuner.options_for_csr(row_ptr.numel() - 1, col_idx.numel()))
         return cc_labels_csr(self._ctx, row_ptr, col_idx, labels)
+
+    def csr64(self, row_ptr, col_idx, labels=None):
+        return cc_labels_csr64(self._ctx, row_ptr, col_idx, labels)
 
     def coo(self, n_vertices, src, dst, labels=None):
         return cc_labels_coo(self._ctx, n_vertices, src, dst, labels)
 
     def batched(self, v_off, a_off, row_ptr_cat, col_idx_cat, labels=None, graph_status=None):
+        if self.tuner is not None:
+            n = v_off.numel() - 1
+            self._apply_tuned(self.tuner.options_for_batch(n, row_ptr_cat.numel() - n, col_idx_cat.numel()))
         return cc_labels_batched(self._ctx, v_off, a_off, row_ptr_cat, col_idx_cat, labels, graph_status)
 
     def csr_host(self, row_ptr, col_idx, labels=None):

@@ -109,13 +109,19 @@ constexpr int kPlainBlock = 256;   // default block of the plain hook
 constexpr int kTiledBlock = 1024;  // default block of the two-phase hook
 constexpr int kPhaseABlock = 1024; // default block of its phase-A launch
 constexpr int kSampleThreads = 16384;
-constexpr double kLocalFractionForTiles = 0.5;
+constexpr double kLocalFractionForTiles = 0.5;     // cc_options.auto_local_permille = 0
 // Automatic choice of the sampled-and-filtered hook (CC_FLAG_SYMMETRIC, no locality): at least
 // this fraction of sampled rows has a degree below a quarter of the mean, as in power-law graphs
 // whose arcs sit mostly in the long rows of a giant component. (On R-MAT the filter skips most
 // arcs; on ER graphs, with no such skew, the first slice costs more than the plain hook.)
-constexpr double kLowDegreeFractionForFilter = 0.25;
+constexpr double kLowDegreeFractionForFilter = 0.25;  // cc_options.auto_lowdeg_permille = 0
+constexpr long long kAutoMinVertices = 1 << 17;      // cc_options.auto_min_vertices = 0
 constexpr int kPhaseSlots = 64;
+// Automatic choice of the cluster kernel (CC_MODE_AUTO, CSR) up to cc_options.cluster_max_vertices
+// vertices (0 = never: on GB300 the grid-wide kernels measured faster on most small graphs, the
+// cluster kernel on some power-law ones, so the choice is left to the autotuner) and
+// kClusterAutoMaxArcs arcs per 2^18 vertices.
+constexpr long long kClusterAutoMaxArcs = 1 << 23;
 
 // Makes `device` current for the scope of a call and restores the caller's device after.
 struct DeviceGuard {
@@ -180,7 +186,8 @@ int balanced_window(const cc_ctx* ctx, cc::Problem p, int block) {
 cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out, bool* skewed_out) {
   *w_out = 0;
   *skewed_out = false;
-  if (p.V < 2 * 65536) return CC_OK;  // small graphs: the plain hook
+  const cc_options& o = ctx->opt;
+  if (p.V < (o.auto_min_vertices > 0 ? (long long)o.auto_min_vertices : kAutoMinVertices)) return CC_OK;  // plain hook
   const int w = window_for(p.V, kDefaultTileVertices);
   if (ctx->auto_rp == p.rp && ctx->auto_col == p.col && ctx->auto_V == p.V && ctx->auto_m == p.m) {
     *w_out = ctx->auto_w;
@@ -207,23 +214,29 @@ cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out, bool* skewe
   ctx->auto_col = p.col;
   ctx->auto_V = p.V;
   ctx->auto_m = p.m;
-  ctx->auto_w = frac >= kLocalFractionForTiles ? w : 0;
+  const double local_min = o.auto_local_permille > 0 ? o.auto_local_permille / 1000.0 : kLocalFractionForTiles;
+  const double lowdeg_min = o.auto_lowdeg_permille > 0 ? o.auto_lowdeg_permille / 1000.0 : kLowDegreeFractionForFilter;
+  ctx->auto_w = frac >= local_min ? w : 0;
   const double rows = (double)ctx->h_sample[3];
-  ctx->auto_skewed = rows > 0 && (double)ctx->h_sample[2] / rows >= kLowDegreeFractionForFilter;
+  ctx->auto_skewed = rows > 0 && (double)ctx->h_sample[2] / rows >= lowdeg_min;
   *w_out = ctx->auto_w;
   *skewed_out = ctx->auto_skewed;
   return CC_OK;
 }
 
 bool options_ok(const cc_options* o) {
-  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_FILTERED) return false;
+  if (o->mode < CC_MODE_AUTO || o->mode > CC_MODE_CLUSTER) return false;
   if (o->segments < -1 || o->grid_blocks < 0) return false;
   if (o->chunk_arcs < -1 || (o->chunk_arcs > 0 && o->chunk_arcs % 32 != 0)) return false;
   if (o->tile_vertices != 0 && o->tile_vertices != -1 &&
       (o->tile_vertices < 256 || o->tile_vertices > kMaxTileVertices ||
        (o->tile_vertices & (o->tile_vertices - 1)) != 0))
     return false;
-  if (o->sm_limit < 0 || o->stream_arcs < 0) return false;
+  if (o->sm_limit < 0 || o->stream_arcs < 0 || o->reserved != 0) return false;
+  if (o->hook_k != 0 && o->hook_k != 1 && o->hook_k != 2 && o->hook_k != 4) return false;
+  if (o->auto_min_vertices < 0 || o->auto_local_permille < 0 || o->auto_local_permille > 1000 ||
+      o->auto_lowdeg_permille < 0 || o->auto_lowdeg_permille > 1000 || o->cluster_max_vertices < 0)
+    return false;
   if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0)) return false;
   if (o->flags & ~(CC_FLAG_SYMMETRIC | CC_FLAG_VALIDATE | CC_FLAG_SYNC | CC_FLAG_PHASE_TIMES)) return false;
   return true;
@@ -344,6 +357,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   c.timeout_ns = o.timeout_ns;
   c.skip_arrival_block = -1;
   c.chunk_arcs = o.chunk_arcs;
+  c.hook_k = o.hook_k > 0 ? o.hook_k : 1;
 
   // Work-proportional grid, capped by what is co-resident (the persistent kernel needs it).
   const long long work = std::max<long long>(p.V, p.m / 4);
@@ -368,6 +382,16 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
   }
 
   info.block = block;
+  const long long cluster_max_v = o.cluster_max_vertices;
+  const bool want_cluster =
+      p.kind == cc::kKindCsr && p.m > 0 &&
+      (o.mode == CC_MODE_CLUSTER || (o.mode == CC_MODE_AUTO && o.tile_vertices == 0 && p.V <= cluster_max_v &&
+                                     p.m <= kClusterAutoMaxArcs * std::max<long long>(1, cluster_max_v >> 18)));
+  const int cluster = want_cluster ? cc::cluster_size_for(p) : 0;
+  if (o.mode == CC_MODE_CLUSTER && cluster == 0) {
+    std::snprintf(ctx->last_error, sizeof(ctx->last_error), "graph does not fit one thread-block cluster");
+    return CC_ERR_INVALID_ARG;
+  }
   // Per-call status: the per-launch fields of the status block (validation's abort flag
   // included) and the caller's status output start at zero.
   {
@@ -381,6 +405,33 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     cudaError_t e = cc::launch_validate(p, c, vs, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "validate launch");
     info.launches += 1;
+  }
+
+  if (cluster > 0) {
+    cudaError_t e = cudaSuccess;
+    if (o.flags & CC_FLAG_PHASE_TIMES) {
+      if (!ctx->d_phase && cudaMalloc(&ctx->d_phase, kPhaseSlots * sizeof(unsigned long long)) != cudaSuccess) {
+        ctx->d_phase = nullptr;
+        cudaGetLastError();
+        return CC_ERR_OOM;
+      }
+      e = cudaMemsetAsync(ctx->d_phase, 0, kPhaseSlots * sizeof(unsigned long long), ctx->stream);
+      c.phase_ns = ctx->d_phase;
+      c.phase_cap = kPhaseSlots;
+      ctx->phase_valid = true;
+    } else {
+      ctx->phase_valid = false;
+    }
+    if (e == cudaSuccess) e = cc::launch_cluster(p, c, cluster, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cluster launch");
+    info.mode = CC_MODE_CLUSTER;
+    info.segments = p.sym ? 2 : 1;
+    info.grid_blocks = cluster;
+    info.block = 1024;
+    info.launches += 1;
+    ctx->last = info;
+    if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
+    return CC_OK;
   }
 
   // Two-phase hierarchical hook (CSR, persistent mode): windows of W vertices.
@@ -618,6 +669,45 @@ cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const v
   p.m = n_arcs;
   p.sym = (ctx->opt.flags & CC_FLAG_SYMMETRIC) != 0;
   return run_problem(ctx, p);
+}
+
+cc_status cc_labels_csr64(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const int64_t* row_ptr,
+                          const int64_t* col_idx, int64_t* labels) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (n_vertices < 0 || n_vertices > (INT64_MAX >> 4) || n_arcs < 0 || n_arcs > (INT64_MAX >> 4)) return CC_ERR_INVALID_ARG;
+  if (!row_ptr || (n_vertices > 0 && !labels) || (n_arcs > 0 && (!col_idx || n_vertices == 0))) return CC_ERR_INVALID_ARG;
+  const size_t lab_bytes = (size_t)n_vertices * 8;
+  if (overlaps(labels, lab_bytes, row_ptr, (size_t)(n_vertices + 1) * 8) ||
+      overlaps(labels, lab_bytes, col_idx, (size_t)n_arcs * 8))
+    return CC_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return CC_ERR_CUDA;
+  ctx->last = cc_run_info{};
+  if (n_vertices == 0) return finish_empty_call(ctx);
+  const cc_options& o = ctx->opt;
+  cc::Ctl c;
+  c.st = ctx->d_status;
+  c.timeout_ns = o.timeout_ns;
+  c.status_out = ctx->status_out;
+  cudaError_t e = cudaMemsetAsync(ctx->d_status, 0, cc::kPerLaunchStatusBytes, ctx->stream);
+  if (e == cudaSuccess && ctx->status_out) e = cudaMemsetAsync(ctx->status_out, 0, sizeof(int32_t), ctx->stream);
+  const bool sym = (o.flags & CC_FLAG_SYMMETRIC) != 0;
+  const int per_sm = std::max(1, cc::wide_blocks_per_sm(sym));
+  const long long want = std::max<long long>(1, (std::max(n_vertices, n_arcs / 4) + 255) / 256);
+  const int grid = (int)std::min<long long>(want, (long long)per_sm * usable_sms(ctx));
+  if (e == cudaSuccess)
+    e = cc::launch_wide(reinterpret_cast<const long long*>(row_ptr), reinterpret_cast<const long long*>(col_idx),
+                        reinterpret_cast<long long*>(labels), n_vertices, n_arcs, sym, c, grid, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "64-bit labelling");
+  cc_run_info info{};
+  info.mode = CC_MODE_MULTI_LAUNCH;
+  info.segments = 1;
+  info.grid_blocks = grid;
+  info.block = 256;
+  info.launches = 3;
+  ctx->last = info;
+  if (o.flags & CC_FLAG_SYNC) return read_and_clear_status(ctx);
+  return CC_OK;
 }
 
 cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const int32_t* src, const int32_t* dst,

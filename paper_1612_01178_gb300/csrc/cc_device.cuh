@@ -65,6 +65,7 @@ struct Ctl {
   int* ovf_units = nullptr;               // windows whose worklist appends overflowed
   int ovf_cap = 0;
   int segments_b = 0;                     // segments of the global phase (0 = 2|E'|/|V|)
+  int hook_k = 1;                         // arcs per lane per step of the plain CSR hook: 1, 2 or 4
   int window_mode = 0;                    // batched: kWindowsSampled or kWindowsPlain
   int* status_out = nullptr;              // optional per-call input status (CC_ERR_OUT_OF_RANGE or left 0)
   unsigned long long* phase_ns = nullptr; // optional per-barrier timestamps (block 0)
@@ -601,21 +602,34 @@ __device__ __forceinline__ void sink_flush(WarpSink& s, const Ctl& c) {
   s.count = 0;
 }
 
-// One step of the local hook of (a, b) that needs no root walk: done if a and b have the same
-// parent; else, if one of them is a root whose ID is above the other's parent, a CAS links it
-// to that parent (an ancestor of the other endpoint, so the invariant lp(x) <= x holds and the
-// two trees are joined). Returns false when the hook is left for local_hook.
+// The local hook of (a, b) when it needs no root walk: done if a and b have the same parent or
+// the same grandparent; else, if a parent is a root (its own parent) whose ID is above the other
+// endpoint's grandparent, or both parents are roots, a CAS links that root to the other
+// grandparent (or the larger root to the smaller): an ancestor of the other endpoint, so the
+// invariant lp(x) <= x holds and the two trees are joined. Returns false when the hook is left for
+// local_hook.
 template <typename LT>
 __device__ __forceinline__ bool local_hook_try(LT* lp, int a, int b) {
-  const int pa = reinterpret_cast<volatile LT*>(lp)[a];
-  const int pb = reinterpret_cast<volatile LT*>(lp)[b];
-  const bool link_b = pb == b && b > pa;
-  const bool link_a = pa == a && a > pb;
-  const int H = link_b ? b : a;
-  const int L = link_b ? pa : pb;
-  bool done = pa == pb;
-  if (!done && (link_a || link_b)) done = cas_local(lp + H, H, L) == H;
-  return done;
+  volatile LT* vl = lp;
+  const int pa = vl[a], pb = vl[b];
+  if (pa == pb) return true;
+  const int ga = vl[pa], gb = vl[pb];
+  if (ga == gb) return true;
+  const bool ra = pa == ga, rb = pb == gb;  // pa / pb is a root
+  int H, L;
+  if (ra && rb) {
+    H = pa > pb ? pa : pb;
+    L = pa > pb ? pb : pa;
+  } else if (rb && pb > ga) {
+    H = pb;
+    L = ga;
+  } else if (ra && pa > gb) {
+    H = pa;
+    L = gb;
+  } else {
+    return false;
+  }
+  return cas_local(lp + H, H, L) == H;
 }
 
 // Queues the hooks that local_hook_try left (lanes with `take`) and finishes 32 of them, one per
@@ -681,6 +695,7 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
   int r = warp_row_search<OffT>(rp, lo_row, V, t0);
   int rc = -1;  // row whose end ec is cached by resolve_row
   OffT ec = 0;
+  long long bad_at = -1;  // an arc with an endpoint outside [0, V), reported after the loop
   int vn[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -713,10 +728,7 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
         u[j] = resolve_row<OffT>(rp, V, r, valid ? a : bj, valid, rem < 31 ? (int)rem : 31, rc, ec);
         if (valid) {
           const bool in_range = (unsigned)v[j] < (unsigned)V && (unsigned)u[j] < (unsigned)V;
-          if (!in_range) {
-            raise_input_error(c, kSiteHookArc, (long long)a);
-            if (bad) *bad = 1;
-          }
+          bad_at = in_range ? bad_at : (long long)a;
           live[j] = in_range && !(SYM ? (u[j] >= v[j]) : (u[j] == v[j]));
         }
       }
@@ -748,10 +760,24 @@ __device__ __forceinline__ void hook_csr_range(const OffT* __restrict__ rp, cons
       atomic_hook_k<K>(pi, u, v, live, vbase + V, c);
     }
   }
+  if (bad_at >= 0) {
+    raise_input_error(c, kSiteHookArc, bad_at);
+    if (bad) *bad = 1;
+  }
 }
 
-constexpr int kHookK = 1;   // arcs per lane per step of the plain hook
+constexpr int kHookK = 1;   // default arcs per lane per step of the plain hook (Ctl::hook_k)
 constexpr int kPairK = 4;   // worklist pairs per thread per step of phase B
+
+// hook_csr_range with c.hook_k arcs per lane per step (an autotuned choice: more arcs in flight per
+// lane against fewer lanes' worth of registers).
+template <typename OffT, bool SYM, int HOOK>
+__device__ __forceinline__ void hook_csr_range_k(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
+                                                 int V, OffT t0, OffT t1, const Ctl& c) {
+  if (HOOK == kHookAtomic && c.hook_k == 2) hook_csr_range<OffT, SYM, 2, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+  else if (HOOK == kHookAtomic && c.hook_k == 4) hook_csr_range<OffT, SYM, 4, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+  else hook_csr_range<OffT, SYM, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+}
 
 // Atomic-Hook over the arcs [a0, a1) of a CSR graph (one segment E_i of Fig. 4). With
 // c.chunk_arcs > 0, warps take chunks of that many arcs from the work counter `ctr` (zeroed
@@ -767,7 +793,7 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     const long long warp = tid >> 5, nwarps = nthreads >> 5;
     const OffT t0 = a0 + split_point<OffT>(len, nwarps, warp);
     const OffT t1 = a0 + split_point<OffT>(len, nwarps, warp + 1);
-    if (t0 < t1) hook_csr_range<OffT, SYM, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+    if (t0 < t1) hook_csr_range_k<OffT, SYM, HOOK>(rp, col, pi, V, t0, t1, c);
     return;
   }
   const OffT C = (OffT)c.chunk_arcs;
@@ -780,7 +806,7 @@ __device__ __forceinline__ void hook_csr_arcs(const OffT* __restrict__ rp, const
     if (t >= n_chunks) break;
     const OffT t0 = a0 + (OffT)t * C;
     const OffT t1 = (len - (OffT)t * C) > C ? t0 + C : a1;
-    hook_csr_range<OffT, SYM, kHookK, HOOK>(rp, col, pi, V, t0, t1, c, 0);
+    hook_csr_range_k<OffT, SYM, HOOK>(rp, col, pi, V, t0, t1, c);
   }
 }
 
@@ -801,13 +827,13 @@ constexpr int kGiantSamples = 256;
 template <typename OffT>
 __device__ __forceinline__ void hook_row_heads(const OffT* __restrict__ rp, const int* __restrict__ col, int* pi,
                                                int V, OffT nnz, long long tid, long long nthreads, const Ctl& c) {
+  long long bad_at = -1;  // a row with bad offsets or an arc outside [0, V), reported after the loop
   for (long long x = tid; x < V; x += nthreads) {
     const int u = (int)x;
     OffT a0 = ld_ro(rp + u), a1 = ld_ro(rp + u + 1);
-    if (!(a0 >= 0 && a0 <= a1 && a1 <= nnz)) {
-      raise_input_error(c, kSiteHookArc, (long long)u);
-      a1 = a0;
-    }
+    const bool span_ok = a0 >= 0 && a0 <= a1 && a1 <= nnz;
+    bad_at = span_ok ? bad_at : (long long)u;
+    a1 = span_ok ? a1 : a0;
     int uu[kSampleArcs], v[kSampleArcs];
     bool live[kSampleArcs];
 #pragma unroll
@@ -815,12 +841,13 @@ __device__ __forceinline__ void hook_row_heads(const OffT* __restrict__ rp, cons
       const bool has = (long long)a0 + j < (long long)a1;
       v[j] = has ? ld_stream(col + a0 + j) : 0;
       const bool in_range = (unsigned)v[j] < (unsigned)V;
-      if (has && !in_range) raise_input_error(c, kSiteHookArc, (long long)a0 + j);
+      bad_at = (has && !in_range) ? (long long)a0 + j : bad_at;
       live[j] = has && in_range && v[j] != u;
       uu[j] = u;
     }
     atomic_hook_k<kSampleArcs>(pi, uu, v, live, V, c);
   }
+  if (bad_at >= 0) raise_input_error(c, kSiteHookArc, bad_at);
 }
 
 // The most frequent root among n = min(kGiantSamples, blockDim.x) vertices spread over [0, V),
@@ -858,6 +885,7 @@ __device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, c
                                                   const Ctl& c) {
   const int lane = threadIdx.x & 31;
   const long long warp = tid >> 5, nwarps = nthreads >> 5;
+  long long bad_at = -1;  // an arc outside [0, V), reported after the loop
   for (long long base = warp * 32; base < V; base += nwarps * 32) {  // warp-uniform
     const long long x = base + lane;
     const int u = (int)x;
@@ -872,11 +900,9 @@ __device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, c
     if (!heavy) {
       for (long long a = a0; a < a1; ++a) {
         const int v = ld_stream(col + a);
-        if ((unsigned)v >= (unsigned)V) {
-          raise_input_error(c, kSiteHookArc, a);
-          continue;
-        }
-        if (v != u) atomic_hook(pi, u, v, V, c);
+        const bool in_range = (unsigned)v < (unsigned)V;
+        bad_at = in_range ? bad_at : a;
+        if (in_range && v != u) atomic_hook(pi, u, v, V, c);
       }
     }
     unsigned hv = __ballot_sync(kFull, heavy);
@@ -890,13 +916,14 @@ __device__ __forceinline__ void hook_rows_outside(const OffT* __restrict__ rp, c
         const bool has = a < h1;
         const int v = has ? ld_stream(col + a) : 0;
         const bool in_range = (unsigned)v < (unsigned)V;
-        if (has && !in_range) raise_input_error(c, kSiteHookArc, a);
+        bad_at = (has && !in_range) ? a : bad_at;
         const int uu[1] = {hu}, vv[1] = {v};
         const bool live[1] = {has && in_range && v != hu};
         atomic_hook_k<1>(pi, uu, vv, live, V, c);
       }
     }
   }
+  if (bad_at >= 0) raise_input_error(c, kSiteHookArc, bad_at);
 }
 
 // Bytes of dynamic shared memory of phase A for a block of `block` threads: the window's parent
@@ -962,17 +989,19 @@ __device__ __forceinline__ void load_group(const int* __restrict__ col, OffT x0,
 // Phase A work for one arc (u, v) of window [w0, w0 + nrows), u = w0 + i in the window. IDs
 // are local to the graph (< V); worklist entries get vbase added (the graph's first vertex in a
 // batch). An endpoint outside [0, V) is only flagged here (no branch on the hot path);
-// phase_a_window reports it once per window.
+// phase_a_window reports it once per window. ia >= 0: the arc to u + 1 is hooked from local row
+// ia instead of i (the first row of the run of u -> u + 1 arcs that reaches u).
 template <bool SYM, typename LT>
 __device__ __forceinline__ void phase_a_arc(bool has, int i, int u, int v, int V, int w0, int nrows, LT* lp,
-                                            WarpSink& sink, int vbase, const Ctl& c) {
+                                            WarpSink& sink, int vbase, const Ctl& c, int ia = -1) {
   const bool in_range = has && (unsigned)v < (unsigned)V;
   sink.flags = (has && !in_range) ? ((sink.flags & kSinkOverflow) | kSinkBadArc | ((i + 1) << 2)) : sink.flags;
   const bool live = in_range && (SYM ? (v > u) : (v != u));
   const int b = v - w0;
   const bool local = live && (unsigned)b < (unsigned)nrows;
-  const bool left = local && !local_hook_try(lp, i, b);
-  defer_push(sink, left, i, b, lp);
+  const int a = (ia >= 0 && v == u + 1) ? ia : i;
+  const bool left = local && !local_hook_try(lp, a, b);
+  defer_push(sink, left, a, b, lp);
   sink_push(sink, live && !local, u + vbase, v + vbase, c);
 }
 
@@ -1011,9 +1040,20 @@ __device__ __forceinline__ void phase_a_window(const OffT* __restrict__ rp, cons
       const int u = w0 + i;
       const long long deg = (long long)(a1 - a0);
       const bool heavy = deg > kHeavyRow;
+      // Arcs u -> u + 1 inside the warp's 32 rows form runs of consecutive rows; the arc into row
+      // u + 1 is hooked from the run's first row instead (the same tree joined through the run),
+      // so a run becomes one star rather than a chain of parents.
+      bool right = false;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) right |= (!heavy && j < deg && v[j] == u + 1);
+      right = right && lane < 31 && i + 1 < nrows;
+      const unsigned rmask = __ballot_sync(kFull, right);
+      const unsigned below = ~rmask & ((2u << lane) - 1u);
+      const int run0 = below ? 32 - __clz(below) : 0;
+      const int ia = right ? i - lane + run0 : -1;
 #pragma unroll
       for (int j = 0; j < kGroup; ++j)
-        phase_a_arc<SYM, LT>(!heavy && j < deg, i, u, v[j], V, w0, nrows, lp, sink, vbase, c);
+        phase_a_arc<SYM, LT>(!heavy && j < deg, i, u, v[j], V, w0, nrows, lp, sink, vbase, c, ia);
       const int maxdeg = __reduce_max_sync(kFull, heavy ? 0 : (int)deg);
       for (int g = 1; g * kGroup < maxdeg; ++g) {
         int w[kGroup];
@@ -1224,6 +1264,7 @@ __device__ __forceinline__ void hook_coo_edges(const int* __restrict__ src, cons
                                                int V, long long e0, long long e1, long long tid,
                                                long long nthreads, const Ctl& c) {
   constexpr int K = kHookK;
+  long long bad_at = -1;  // an edge with an endpoint outside [0, V), reported after the loop
   for (long long base = e0 + tid; base < e1; base += nthreads * K) {
     int u[K], v[K];
     bool live[K];
@@ -1234,11 +1275,12 @@ __device__ __forceinline__ void hook_coo_edges(const int* __restrict__ src, cons
       u[j] = valid ? ld_stream(src + i) : 0;
       v[j] = valid ? ld_stream(dst + i) : 0;
       const bool in_range = (unsigned)u[j] < (unsigned)V && (unsigned)v[j] < (unsigned)V;
-      if (valid && !in_range) raise_input_error(c, kSiteHookArc, i);
+      bad_at = (valid && !in_range) ? i : bad_at;
       live[j] = valid && in_range && u[j] != v[j];
     }
     atomic_hook_k<K>(pi, u, v, live, V, c);
   }
+  if (bad_at >= 0) raise_input_error(c, kSiteHookArc, bad_at);
 }
 
 }  // namespace cc

@@ -114,6 +114,20 @@ cudaError_t launch_jump_multi(const Problem& p, const Ctl& c, LaunchShape s, cud
 cudaError_t launch_hook_segment(const Problem& p, const int* col_seg, long long a0, long long a1, const Ctl& c,
                                 LaunchShape s, cudaStream_t stream);
 
+// Small graphs in one thread-block cluster (cc_cluster.cu): pi in the distributed shared memory of
+// C CTAs (8, or 16 where the GPU allows it), at most 2^kClusterMaxShift vertices per CTA.
+constexpr int kClusterMaxShift = 15;
+// Cluster size that can hold p in one cluster of co-resident CTAs, or 0.
+int cluster_size_for(const Problem& p);
+// One launch of C CTAs: writes the labels into p.pi.
+cudaError_t launch_cluster(const Problem& p, const Ctl& c, int C, cudaStream_t stream);
+
+// 64-bit vertex IDs (cc_wide.cu): init, Atomic-Hook of every arc, Multi-Jump; three launches of
+// `grid` blocks on `stream`. wide_blocks_per_sm: co-resident blocks of the hook kernel per SM.
+int wide_blocks_per_sm(bool sym);
+cudaError_t launch_wide(const long long* rp, const long long* col, long long* pi, long long V, long long nnz, bool sym,
+                        const Ctl& c, int grid, cudaStream_t stream);
+
 // Device checks of CSR offsets and endpoints (CC_FLAG_VALIDATE).
 cudaError_t launch_validate(const Problem& p, const Ctl& c, LaunchShape s, cudaStream_t stream);
 

@@ -1,4 +1,5 @@
-"""Autotuner of the launch options (segments s, hook window, block size, hook work split).
+"""Autotuner of the launch options (hook choice and its switch thresholds, segments s, hook
+window, block size, hook work split, arcs per lane).
 
 The best options depend on the graph family and size and on the GPU, so they are measured, not
 guessed: for a graph, a coordinate search times a small set of candidate options through the
@@ -17,13 +18,23 @@ import threading
 
 from . import cc as ccapi
 
-# Candidate values, searched one option at a time (in this order) from the current best.
+# Candidate values, searched one option at a time (in this order) from the current best. The mode
+# and the thresholds of the automatic choice decide which hook runs (cluster, plain, two-phase,
+# sampled-and-filtered); the rest shape the launches of that hook.
 SEARCH = [
+    ("mode", [0, 1, 5, 6]),
     ("tile_vertices", [0, -1, 8192, 16384, 32768]),
+    ("auto_min_vertices", [0, 1 << 15, 1 << 20]),
+    ("auto_local_permille", [0, 300, 700]),
+    ("auto_lowdeg_permille", [0, 100, 500]),
+    ("cluster_max_vertices", [0, 1 << 16, 1 << 18, 1 << 19]),
     ("segments", [0, 1, 2, 4, 8, -1]),
     ("block", [0, 256, 512, 1024]),
     ("chunk_arcs", [0, -1, 1024, 2048]),
+    ("hook_k", [0, 2, 4]),
 ]
+# The batched launch: its window (graphs up to this size stay in one CTA), segments and block.
+SEARCH_BATCHED = [("tile_vertices", [0, 8192, 16384, -1]), ("segments", [0, 1, 2, 4]), ("block", [0, 512, 1024])]
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gb300_cc_tune.json")
 
@@ -61,6 +72,13 @@ class Tuner:
             rec = self.cache.get(key)
         return dict(rec["options"]) if rec else None
 
+    def options_for_csr(self, n_vertices: int, n_arcs: int):
+        """Tuned options of the bucket of a CSR graph with these sizes (any numbering), or None."""
+        return self.lookup(bucket("csr", n_vertices, n_arcs))
+
+    def options_for_batch(self, n_graphs: int, total_vertices: int, total_arcs: int):
+        return self.lookup(bucket(f"batch{int(round(math.log2(max(1, n_graphs))))}", total_vertices, total_arcs))
+
     def search(self, measure, start: dict | None = None, space=SEARCH):
         """Coordinate search: measure(options) -> (ms, labels). Returns (best options, best ms, log).
         Every candidate's labels must equal the first ones (the options only change the speed)."""
@@ -76,7 +94,7 @@ class Tuner:
                 try:
                     ms, labels = measure(cand)
                 except ccapi.CCError:
-                    continue  # e.g. a block size that cannot be co-resident with this window
+                    continue  # e.g. a block size that cannot be co-resident, or a graph too large for one cluster
                 if ref is not None and labels is not None and not _same(labels, ref):
                     raise AssertionError(f"options {cand} changed the labels")
                 log.append((dict(cand), ms))
@@ -109,7 +127,7 @@ class Tuner:
         total_v = row_ptr_cat.numel() - n
         key = key or bucket(f"batch{int(round(math.log2(max(1, n))))}", total_v, col_idx_cat.numel())
         labels = torch.empty(total_v, dtype=torch.int32, device=v_off.device)
-        space = [("tile_vertices", [0, 8192, 16384, -1]), ("segments", [0, 1, 2, 4]), ("block", [0, 512, 1024])]
+        space = SEARCH_BATCHED
 
         def measure(opts):
             with ccapi.ConnectedComponents(v_off.device.index or 0, flags=flags, **opts) as cc:

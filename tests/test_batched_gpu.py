@@ -252,3 +252,22 @@ def test_graph_mixing_local_and_random_windows(dev):
     for tile in (256, 1024):
         got, _ = run_batched(dev, b, tile_vertices=tile, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC)
         assert_batch(got, b, what=f"mixed windows tile={tile}")
+
+
+def test_million_vertex_graphs_among_small_ones(dev):
+    """The batched workload draws graphs of up to 10^6 vertices: a 1000 x 1000 grid (windows with
+    locality) and an R-MAT graph of 2^20 vertices (windows without) among a few hundred small ones,
+    every graph checked against the oracle, symmetric and not."""
+    rng = np.random.default_rng(61)
+    graphs = [gen.grid_csr(1000, 0.9, seed=62), gen.rmat_csr(20, 8, seed=63)]
+    for i in range(300):
+        V = int(rng.integers(1000, 40_000))
+        graphs.append(gen.er_csr(V, int(V * rng.integers(2, 16)), seed=700 + i) if i % 2 else
+                      gen.grid_csr(int(np.sqrt(V)), 0.9, seed=700 + i))
+    order = rng.permutation(len(graphs))
+    b = gen.batch_from_graphs([graphs[i] for i in order])
+    want = expected(b)
+    for flags in (ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC, ccl.CC_FLAG_SYNC):
+        got, st = run_batched(dev, b, status=True, flags=flags)
+        assert (st == 0).all()
+        assert_batch(got, b, want, what=f"flags={flags}")

@@ -35,3 +35,24 @@ def test_search_rejects_options_that_change_labels():
 
     with pytest.raises(AssertionError):
         Tuner(None).search(measure)
+
+
+def test_search_space_names_real_options():
+    from paper_1612_01178_gb300 import cc
+    from paper_1612_01178_gb300.tune import SEARCH, SEARCH_BATCHED
+    fields = {f for f, _ in cc.cc_options._fields_}
+    for name, values in SEARCH + SEARCH_BATCHED:
+        assert name in fields, name
+        assert values and values[0] == 0 or name == "mode"
+    names = [n for n, _ in SEARCH]
+    for knob in ("hook_k", "auto_min_vertices", "auto_local_permille", "auto_lowdeg_permille", "cluster_max_vertices"):
+        assert knob in names
+
+
+def test_bucket_lookup_helpers(tmp_path):
+    t = Tuner(str(tmp_path / "t.json"))
+    t.cache[bucket("csr", 100_000, 2_000_000)] = {"options": {"mode": 6}, "ms": 0.02}
+    assert t.options_for_csr(100_000, 2_000_000) == {"mode": 6}
+    assert t.options_for_csr(100_000, 200) is None
+    t.cache[bucket("batch12", 5_000_000, 60_000_000)] = {"options": {"block": 512}, "ms": 9.0}
+    assert t.options_for_batch(4096, 5_000_000, 60_000_000) == {"block": 512}

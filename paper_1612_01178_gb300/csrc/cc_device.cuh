@@ -193,16 +193,16 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Root of x's tree. Path halving: each visited vertex whose grandparent differs from its
-// parent is re-pointed at the grandparent, so later walks are shorter. x strictly decreases
-// along the walk (pi(y) < y for non-roots), so it ends within V steps.
+// Root of x's tree, walked two levels per step without writing: the first levels of a hook's
+// walks already halve the path (root_from2), and the stores of a second halving pass measured
+// slower (they contend with the hooks on the few hot vertices near the roots). x strictly
+// decreases along the walk (pi(y) < y for non-roots), so it ends within V steps.
 
 __device__ __forceinline__ int find_root(int* pi, int x) {
   int px = ld_pi(pi + x);
   while (px != x) {
     const int gx = ld_pi(pi + px);
     if (gx == px) return px;
-    st_pi(pi + x, gx);
     x = gx;
     px = ld_pi(pi + x);
   }

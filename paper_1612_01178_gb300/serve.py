@@ -15,14 +15,14 @@ the host. The loop:
      copy-in fails, is rejected with a status (CC_ERR_OOM, CC_ERR_CUDA) and the loop goes on
      serving the others.
   3. The server has `lanes` compute lanes (a stream with its own library contexts each). When a
-     lane is idle, every admitted request not yet launched goes into ONE launch on that lane: a
+     lane is idle, every admitted request not yet launched goes into ONE launch on that lane (on
+     all SMs if the other lanes are idle, else on the lane's share of them): a
      descriptor-mode batched launch (cc_labels_batched_desc) that waits on the requests' copy-in
      events, or, for a batch of at most `single_max` requests, back-to-back single-graph launches
      (cheaper for few graphs), each with the hook its graph calls for (chosen on the host from a
      small sample of the request's degrees and arcs). Requests arriving meanwhile are admitted and
      copied in during those launches and form the next batch, on the other lane if it is idle:
-     batches of two lanes run on the device at the same time (each lane's launches fill at most
-     its share of the SMs).
+     batches of two lanes run on the device at the same time.
   4. With the launch, each request's labels and status are queued for copy-out on the lane's
      stream behind the kernels, into host buffers the request brought (or that the server pins
      for it); once the lane's work is done its requests are complete and their arena slices
@@ -197,11 +197,12 @@ class Server:
         self.arcs = torch.empty(self.caps["arc"], dtype=torch.int32, device=self.dev)
         self.s_in = torch.cuda.Stream(self.dev)
         n_sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
-        share = 0 if self.n_lanes == 1 else max(1, n_sms // self.n_lanes)
+        # A launch fills every SM when the other lanes are idle, else its lane's share of them.
+        self.share = 0 if self.n_lanes == 1 else max(1, n_sms // self.n_lanes)
         self.lanes = []
         for _ in range(self.n_lanes):
             s = torch.cuda.Stream(self.dev)
-            opts = dict(flags=self.flags, sm_limit=share)
+            opts = dict(flags=self.flags, sm_limit=self.share)
             lane = {
                 "stream": s,
                 "batched": ccapi.ConnectedComponents(self.device, stream=s, **opts),
@@ -218,6 +219,7 @@ class Server:
                 "status_host": torch.empty((self.STATUS_BUFFERS, self.max_batch), dtype=torch.int32).pin_memory(),
                 "busy": [0] * self.STATUS_BUFFERS,
                 "running": None,
+                "sm_limit": self.share,
             }
             self.lanes.append(lane)
 
@@ -237,6 +239,15 @@ class Server:
             ev.record(self.s_in)
         return ev
 
+    def _set_share(self, lane, sm_limit: int):
+        """The SMs the lane's launches may fill (0 = all)."""
+        if lane["sm_limit"] == sm_limit:
+            return
+        for key in ("batched", "plain", "tiled", "filtered"):
+            if lane[key] is not None:
+                lane[key].set_options(sm_limit=sm_limit)
+        lane["sm_limit"] = sm_limit
+
     def _launch(self, lane, batch, k):
         """Copies in the requests not yet on the device, labels the batch and queues the copy-out of
         labels and statuses, all on the lane's stream. Returns the event recorded after them."""
@@ -245,6 +256,8 @@ class Server:
         n = len(batch)
         st = lane["status_dev"][k]
         lib = ccapi.load()
+        alone = all(other["running"] is None for other in self.lanes if other is not lane)
+        self._set_share(lane, 0 if alone else self.share)
         for r in batch:
             if r.ev_in is None:
                 self._copy_in(r, stream=s)

@@ -851,7 +851,9 @@ def measure_single(args, ccl, torch, g, name, *, world, rank, local_rank, dist, 
         e2e = {"value": world * g.n_edges / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
                "d2h_bytes_per_step": int(4 * g.n_vertices), "ms_per_step": 1000 * e2e_s,
-               "labels_match": bool(e2e_ok)}
+               # the host link stalls now and then (tens to hundreds of ms); the mean above keeps them
+               "ms_per_step_median": 1000 * statistics.median(tt), "ms_per_step_min": 1000 * min(tt),
+               "steps": n_e2e, "labels_match": bool(e2e_ok)}
         del pin_rp, pin_col, pin_out
 
     peak, peak_kind = measured_peaks()

@@ -155,8 +155,7 @@ typedef struct cc_options {
   int64_t stream_arcs; /* cc_labels_csr_host only: > 0 = leave the arcs in host memory and stream
                           them in segments of this many arcs (see cc_labels_csr_host); -1 = never
                           stream (copy the whole graph, then run the automatic hook); 0 = stream
-                          when the graph does not fit in free device memory, or when it has at
-                          least 2^28 arcs (segments of n_arcs / 16 arcs, 2^25 .. 2^27) */
+                          only when the graph does not fit in free device memory */
   /* Knobs of the automatic choices, for an autotuner (0 = the default in brackets): */
   int32_t hook_k;      /* arcs per lane per step of the plain CSR hook: 1, 2 or 4 [1] */
   int32_t auto_min_vertices;    /* below this many vertices CC_MODE_AUTO keeps the plain hook [2^17] */
@@ -274,10 +273,9 @@ cc_status cc_labels_batched_desc(cc_ctx* ctx, int32_t n_graphs, const cc_graph_d
    returns after the copy completes (always synchronous). The device buffers
    grow to the largest graph seen and are freed by cc_destroy.
    Graphs larger than device memory (Section III-B: the segments bound the
-   working set to the |V|-sized parent array), and large graphs whose copy over
-   the host link outlasts their labelling: when cc_options.stream_arcs > 0, or
-   (stream_arcs = 0) when row_ptr + col_idx + labels do not fit in free device
-   memory or n_arcs >= 2^28, the arcs stay in host memory. row_ptr and the labels (pi) are copied to / kept on the
+   working set to the |V|-sized parent array): when cc_options.stream_arcs > 0,
+   or (stream_arcs = 0) when row_ptr + col_idx + labels do not fit in free
+   device memory, the arcs stay in host memory. row_ptr and the labels (pi) are copied to / kept on the
    device, and Fig. 4 runs with s = ceil(n_arcs / seg) contiguous segments of
    seg arcs (stream_arcs, or two buffers sized from the free memory): segment i
    is copied in on a copy stream while segment i - 1 is Atomic-Hooked (plain

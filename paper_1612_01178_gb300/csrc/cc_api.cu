@@ -893,19 +893,12 @@ static cc_status grow(cc_ctx* ctx, void** buf, size_t* have, size_t need) {
 
 // Arcs per streamed segment for cc_labels_csr_host (0 = copy the whole graph, then label it; -1 =
 // not even row_ptr and labels fit). cc_options.stream_arcs > 0 is taken as given and -1 never
-// streams. Automatically (0): a graph that does not fit in free device memory next to a margin
-// streams through two buffers sized from the memory left after row_ptr and labels; a graph that
-// fits but has at least kStreamMinArcs arcs streams too, in n_arcs / kStreamSegments arcs per
-// segment (within [kStreamMinSegArcs, kStreamMaxSegArcs]): its copy over the host link takes
-// longer than the plain hook of its arcs, so hooking each segment while the next one is copied
-// hides the labelling under the copy.
-// (Measured on GB300: R-MAT 26, 2^31 arcs, 46.5 -> 45.3 ms end to end with 16 segments; the 4096^2
-// grid, 6 * 10^7 arcs, 2.2 -> 2.7 ms with 15 segments, where the Multi-Jumps after every segment
-// outweigh the copy they would hide under.)
-constexpr long long kStreamMinArcs = 1ll << 28;
-constexpr long long kStreamSegments = 16;
-constexpr long long kStreamMinSegArcs = 1ll << 25;
-constexpr long long kStreamMaxSegArcs = 1ll << 27;
+// streams. Automatically (0): only a graph that does not fit in free device memory next to a
+// margin streams, through two buffers sized from the memory left after row_ptr and labels.
+// (Streaming a graph that fits, to hide the labelling under the copy, measured on GB300: R-MAT 26
+// 46.7 -> 45.3 ms per call in the median, but the host link's occasional stalls of 50-180 ms hit
+// the streamed calls more often, 71.8 against 53.9 ms in the mean of 20 calls; the 4096^2 grid
+// 2.2 -> 2.7 ms, the Multi-Jumps after every segment outweighing the copy.)
 static long long stream_segment_arcs(cc_ctx* ctx, size_t rp_bytes, size_t col_bytes, size_t lab_bytes) {
   if (ctx->opt.stream_arcs > 0) return ctx->opt.stream_arcs;
   size_t free_b = 0, total_b = 0;
@@ -916,11 +909,7 @@ static long long stream_segment_arcs(cc_ctx* ctx, size_t rp_bytes, size_t col_by
   const size_t avail = free_b + ctx->d_rp_bytes + ctx->d_col_bytes + ctx->d_labels_bytes +
                        2 * ctx->d_seg_arcs * sizeof(int32_t);  // buffers this call may reuse
   const size_t margin = (size_t)1 << 30;
-  if (rp_bytes + col_bytes + lab_bytes + margin <= avail) {
-    const long long arcs = (long long)(col_bytes / sizeof(int32_t));
-    if (ctx->opt.stream_arcs < 0 || arcs < kStreamMinArcs) return 0;
-    return std::min(kStreamMaxSegArcs, std::max(kStreamMinSegArcs, arcs / kStreamSegments));
-  }
+  if (rp_bytes + col_bytes + lab_bytes + margin <= avail) return 0;
   if (ctx->opt.stream_arcs < 0) return -1;
   const size_t min_seg_bytes = (size_t)1 << 22;
   if (rp_bytes + lab_bytes + margin + 2 * min_seg_bytes > avail) return -1;

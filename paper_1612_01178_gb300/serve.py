@@ -15,8 +15,8 @@ the host. The loop:
      copy-in fails, is rejected with a status (CC_ERR_OOM, CC_ERR_CUDA) and the loop goes on
      serving the others.
   3. The server has `lanes` compute lanes (a stream with its own library contexts each). When a
-     lane is idle, every admitted request not yet launched goes into ONE launch on that lane (on
-     all SMs if the other lanes are idle, else on the lane's share of them): a
+     lane is idle, every admitted request not yet launched goes into ONE launch on that lane (on the
+     lane's share of the SMs): a
      descriptor-mode batched launch (cc_labels_batched_desc) that waits on the requests' copy-in
      events, or, for a batch of at most `single_max` requests, back-to-back single-graph launches
      (cheaper for few graphs), each with the hook its graph calls for (chosen on the host from a
@@ -197,7 +197,9 @@ class Server:
         self.arcs = torch.empty(self.caps["arc"], dtype=torch.int32, device=self.dev)
         self.s_in = torch.cuda.Stream(self.dev)
         n_sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
-        # A launch fills every SM when the other lanes are idle, else its lane's share of them.
+        # Each lane's launches fill its share of the SMs, so the lanes' cooperative launches can be
+        # resident together (a lane alone on every SM measured slower under load: the other lane's
+        # launch then waits for SMs, and batches serialise).
         self.share = 0 if self.n_lanes == 1 else max(1, n_sms // self.n_lanes)
         self.lanes = []
         for _ in range(self.n_lanes):
@@ -219,7 +221,6 @@ class Server:
                 "status_host": torch.empty((self.STATUS_BUFFERS, self.max_batch), dtype=torch.int32).pin_memory(),
                 "busy": [0] * self.STATUS_BUFFERS,
                 "running": None,
-                "sm_limit": self.share,
             }
             self.lanes.append(lane)
 
@@ -239,15 +240,6 @@ class Server:
             ev.record(self.s_in)
         return ev
 
-    def _set_share(self, lane, sm_limit: int):
-        """The SMs the lane's launches may fill (0 = all)."""
-        if lane["sm_limit"] == sm_limit:
-            return
-        for key in ("batched", "plain", "tiled", "filtered"):
-            if lane[key] is not None:
-                lane[key].set_options(sm_limit=sm_limit)
-        lane["sm_limit"] = sm_limit
-
     def _launch(self, lane, batch, k):
         """Copies in the requests not yet on the device, labels the batch and queues the copy-out of
         labels and statuses, all on the lane's stream. Returns the event recorded after them."""
@@ -256,8 +248,6 @@ class Server:
         n = len(batch)
         st = lane["status_dev"][k]
         lib = ccapi.load()
-        alone = all(other["running"] is None for other in self.lanes if other is not lane)
-        self._set_share(lane, 0 if alone else self.share)
         for r in batch:
             if r.ev_in is None:
                 self._copy_in(r, stream=s)

@@ -164,7 +164,9 @@ typedef struct cc_options {
                                    sampled-and-filtered hook [250] */
   int32_t cluster_max_vertices; /* CC_MODE_AUTO runs the cluster kernel up to this many vertices (and
                                    2^23 arcs per 2^18 vertices) [0 = never] */
-  int32_t reserved;    /* must be 0 */
+  int32_t auto_dense_degree;    /* mean degree n_arcs / V from which a symmetric CSR without ID
+                                   locality takes the sampled-and-filtered hook even with unskewed
+                                   degrees, at any size; -1 = only skewed graphs [8] */
 } cc_options;
 
 /* Fills *opt with the defaults (all zero fields resolved as documented above). */

@@ -63,7 +63,7 @@ class cc_options(ctypes.Structure):
         ("auto_local_permille", ctypes.c_int32),
         ("auto_lowdeg_permille", ctypes.c_int32),
         ("cluster_max_vertices", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("auto_dense_degree", ctypes.c_int32),
     ]
 
 

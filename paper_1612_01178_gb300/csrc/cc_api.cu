@@ -112,10 +112,19 @@ constexpr int kSampleThreads = 16384;
 constexpr double kLocalFractionForTiles = 0.5;     // cc_options.auto_local_permille = 0
 // Automatic choice of the sampled-and-filtered hook (CC_FLAG_SYMMETRIC, no locality): at least
 // this fraction of sampled rows has a degree below a quarter of the mean, as in power-law graphs
-// whose arcs sit mostly in the long rows of a giant component. (On R-MAT the filter skips most
-// arcs; on ER graphs, with no such skew, the first slice costs more than the plain hook.)
+// whose arcs sit mostly in the long rows of a giant component (on R-MAT the filter skips most
+// arcs) ...
 constexpr double kLowDegreeFractionForFilter = 0.25;  // cc_options.auto_lowdeg_permille = 0
 constexpr long long kAutoMinVertices = 1 << 17;      // cc_options.auto_min_vertices = 0
+// ... and, at any size, for a symmetric CSR without ID locality whose mean degree n_arcs / V is at
+// least this (cc_options.auto_dense_degree = 0): with the grid barrier's relaxed polling the filter
+// measured faster than the plain hook on ER graphs of mean degree 16 to 40 (ER 100k / 1M 0.090 vs
+// 0.138 ms, ER 16M / 128M 0.65 vs 1.81 ms), slower on sparse ones (ER 20k / 30k 0.065 vs 0.051 ms).
+constexpr int kDenseDegreeForFilter = 8;
+// Block of the sampled-and-filtered hook: 1024-thread CTAs, two per SM, so that each of its grid
+// barriers counts 304 arrivals instead of 1216 (an empty barrier measured 1.7 vs 5.0 us); R-MAT 26
+// 1.72 -> 1.70 ms, ER 100k / 1M 0.105 -> 0.090 ms.
+constexpr int kFilterBlock = 1024;
 constexpr int kPhaseSlots = 64;
 // Automatic choice of the cluster kernel (CC_MODE_AUTO, CSR) up to cc_options.cluster_max_vertices
 // vertices (0 = never: on GB300 the grid-wide kernels measured faster on most small graphs, the
@@ -179,7 +188,8 @@ int balanced_window(const cc_ctx* ctx, cc::Problem p, int block) {
 // Automatic hook choice (tile_vertices = 0): the two-phase hook pays off when most arcs join
 // vertices of the same window, i.e. when the vertex numbering has locality (meshes, road
 // networks in their natural order); otherwise the plain hook is used, or, for a symmetric CSR
-// whose sampled degrees are skewed (*skewed_out), the sampled-and-filtered hook. A small
+// whose sampled degrees are skewed (*skewed_out) or whose mean degree is high (the caller's
+// test, which needs no sample), the sampled-and-filtered hook. A small
 // sampling kernel measures both on the first call for a given graph (row_ptr, col_idx, V,
 // n_arcs); the answers are kept and reused while those stay the same. Only the speed depends
 // on them.
@@ -187,7 +197,7 @@ cc_status auto_window(cc_ctx* ctx, const cc::Problem& p, int* w_out, bool* skewe
   *w_out = 0;
   *skewed_out = false;
   const cc_options& o = ctx->opt;
-  if (p.V < (o.auto_min_vertices > 0 ? (long long)o.auto_min_vertices : kAutoMinVertices)) return CC_OK;  // plain hook
+  if (p.V < (o.auto_min_vertices > 0 ? (long long)o.auto_min_vertices : kAutoMinVertices)) return CC_OK;  // no sample
   const int w = window_for(p.V, kDefaultTileVertices);
   if (ctx->auto_rp == p.rp && ctx->auto_col == p.col && ctx->auto_V == p.V && ctx->auto_m == p.m) {
     *w_out = ctx->auto_w;
@@ -232,7 +242,7 @@ bool options_ok(const cc_options* o) {
       (o->tile_vertices < 256 || o->tile_vertices > kMaxTileVertices ||
        (o->tile_vertices & (o->tile_vertices - 1)) != 0))
     return false;
-  if (o->sm_limit < 0 || o->stream_arcs < -1 || o->reserved != 0) return false;
+  if (o->sm_limit < 0 || o->stream_arcs < -1 || o->auto_dense_degree < -1) return false;
   if (o->hook_k != 0 && o->hook_k != 1 && o->hook_k != 2 && o->hook_k != 4) return false;
   if (o->auto_min_vertices < 0 || o->auto_local_permille < 0 || o->auto_local_permille > 1000 ||
       o->auto_lowdeg_permille < 0 || o->auto_lowdeg_permille > 1000 || o->cluster_max_vertices < 0)
@@ -442,12 +452,15 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
       w = window_for(p.V, o.tile_vertices);
     } else if (o.tile_vertices == 0) {
       bool skewed = false;
+      const int dense_deg = o.auto_dense_degree == 0 ? kDenseDegreeForFilter : o.auto_dense_degree;
+      const bool dense = dense_deg > 0 && p.m >= (long long)dense_deg * p.V;
       const cc_status st = auto_window(ctx, p, &w, &skewed);
       if (st != CC_OK) return st;
       if (w > 0) {
         w = balanced_window(ctx, p, o.block > 0 ? o.block : kPhaseABlock);
-      } else if (skewed && p.sym && o.mode == CC_MODE_AUTO) {
-        // no locality, skewed degrees: the sampled-and-filtered hook (one cooperative launch)
+      } else if (p.sym && o.mode == CC_MODE_AUTO && (skewed || dense)) {
+        // no locality, skewed degrees or a high mean degree: the sampled-and-filtered hook (one
+        // cooperative launch)
         p.filtered = true;
         p.segments = 2;
         info.segments = 2;
@@ -475,6 +488,7 @@ cc_status run_problem(cc_ctx* ctx, cc::Problem& p) {
     c.segments_b = o.segments > 0 ? o.segments : 0;
   }
 
+  if (p.filtered && o.block <= 0) block = kFilterBlock;
   if (mode == CC_MODE_PERSISTENT) {
     // The requested block size must be co-resident at least once per SM; halve it until it is
     // (a kernel variant may need more registers or shared memory than the request allows).

@@ -105,12 +105,6 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   return v;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -170,8 +164,13 @@ __device__ __forceinline__ bool grid_sync(const Ctl& c, unsigned& epoch) {
     if (!skip) red_release_add(&c.st->bar, 1u);
     int go = 1;
     const unsigned long long t0 = now_ns();
+    // The wait polls with relaxed loads and sleeps briefly between polls; the fence after the
+    // loop makes it an acquire. An acquire load inside the loop measured slower: blocks that
+    // reach the barrier early slowed the blocks still hooking on the same SMs (ER 262k / 4M:
+    // first hook slice 168 -> 64 us).
     for (unsigned spin = 0;; ++spin) {
-      if (ld_acquire(&c.st->bar) >= target) break;
+      if ((unsigned)ld_relaxed(reinterpret_cast<const int*>(&c.st->bar)) >= target) break;
+      __nanosleep(64);
       if (launch_blocked(c)) {
         go = 0;
         break;

@@ -129,10 +129,13 @@ class Request:
 
 # The library's automatic choice of a hook needs a sampling kernel and a synchronisation per new
 # graph; a serving loop decides on the host from the request's own arrays instead, with the same
-# rules: below 2^17 vertices the plain hook; if most sampled arcs join two vertices of one
-# 16384-vertex window, the two-phase hook; else, if a quarter of the sampled rows have a degree
-# below a quarter of the mean (a skewed, power-law-like graph), the sampled-and-filtered hook.
+# rules: a symmetric graph of mean degree n_arcs / V >= 8 below 2^17 vertices takes the
+# sampled-and-filtered hook, any other graph that small the plain hook; from 2^17 vertices on, if
+# most sampled arcs join two vertices of one 16384-vertex window, the two-phase hook; else, if the
+# graph is symmetric and a quarter of the sampled rows have a degree below a quarter of the mean
+# (a skewed, power-law-like graph) or its mean degree is >= 8, the sampled-and-filtered hook.
 HOOK_MIN_VERTICES = 1 << 17
+HOOK_DENSE_DEGREE = 8
 HOOK_WINDOW = 16384
 HOOK_SAMPLES = 256
 
@@ -140,8 +143,11 @@ HOOK_SAMPLES = 256
 def choose_hook(row_ptr: np.ndarray, col: np.ndarray, symmetric: bool = True) -> str:
     V = row_ptr.shape[0] - 1
     nnz = col.shape[0]
-    if V < HOOK_MIN_VERTICES or nnz == 0:
+    dense = symmetric and nnz >= HOOK_DENSE_DEGREE * V
+    if nnz == 0:
         return "plain"
+    if V < HOOK_MIN_VERTICES:
+        return "filtered" if dense else "plain"
     u = np.linspace(0, V - 1, HOOK_SAMPLES).astype(np.int64)
     a0 = row_ptr[u].astype(np.int64)
     a1 = row_ptr[u + 1].astype(np.int64)
@@ -155,7 +161,7 @@ def choose_hook(row_ptr: np.ndarray, col: np.ndarray, symmetric: bool = True) ->
     if sampled.sum() and local.sum() >= 0.5 * sampled.sum():
         return "tiled"
     low = (4.0 * (a1 - a0) * V < nnz) & (a0 <= a1)
-    if symmetric and low.mean() >= 0.25:
+    if symmetric and (low.mean() >= 0.25 or dense):
         return "filtered"
     return "plain"
 

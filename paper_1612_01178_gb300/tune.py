@@ -27,6 +27,7 @@ SEARCH = [
     ("auto_min_vertices", [0, 1 << 15, 1 << 20]),
     ("auto_local_permille", [0, 300, 700]),
     ("auto_lowdeg_permille", [0, 100, 500]),
+    ("auto_dense_degree", [0, -1, 4, 16]),
     ("cluster_max_vertices", [0, 1 << 16, 1 << 18, 1 << 19]),
     ("segments", [0, 1, 2, 4, 8, -1]),
     ("block", [0, 256, 512, 1024]),

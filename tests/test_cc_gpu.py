@@ -223,10 +223,14 @@ def test_grid_4096_road(dev):
 def test_automatic_window_choice(dev):
     """Automatic hook choice: the grid (ID locality) gets the two-phase hook (two launches) with a
     balanced window, a multiple of 256 in [2048, 18432]; a randomly numbered R-MAT graph (skewed
-    degrees) gets the sampled-and-filtered hook and an ER graph the plain hook (one launch each)."""
+    degrees) and an ER graph of mean degree 20 get the sampled-and-filtered hook, a sparse ER graph
+    (mean degree 4) and a small sparse one the plain hook (one launch each)."""
     cases = ((gen.grid_csr(1500, 0.9, seed=11), True, ccl.CC_MODE_PERSISTENT),
              (gen.rmat_csr(18, 8, seed=12), False, ccl.CC_MODE_FILTERED),
-             (gen.er_csr(300_000, 3_000_000, seed=13), False, ccl.CC_MODE_PERSISTENT))
+             (gen.er_csr(300_000, 3_000_000, seed=13), False, ccl.CC_MODE_FILTERED),
+             (gen.er_csr(300_000, 600_000, seed=14), False, ccl.CC_MODE_PERSISTENT),
+             (gen.er_csr(20_000, 30_000, seed=15), False, ccl.CC_MODE_PERSISTENT),
+             (gen.er_csr(50_000, 500_000, seed=16), False, ccl.CC_MODE_FILTERED))
     for g, tiled, mode in cases:
         want = expect(g.row_ptr, g.col)
         with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC) as cc:

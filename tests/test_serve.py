@@ -187,11 +187,16 @@ def test_admission_waits_for_memory_in_fifo_order():
 
 
 def test_host_hook_choice():
-    assert choose_hook(*(lambda g: (g.row_ptr, g.col))(gen.er_csr(1000, 5000, seed=1))) == "plain"  # small
+    assert choose_hook(*(lambda g: (g.row_ptr, g.col))(gen.er_csr(1000, 2000, seed=1))) == "plain"  # small, sparse
     grid = gen.grid_csr(600, 0.9, seed=1)
     assert choose_hook(grid.row_ptr, grid.col) == "tiled"
     rm = gen.rmat_csr(18, 8, seed=1)
     assert choose_hook(rm.row_ptr, rm.col) == "filtered"
     assert choose_hook(rm.row_ptr, rm.col, symmetric=False) == "plain"
-    er = gen.er_csr(1 << 18, 1 << 21, seed=2)
-    assert choose_hook(er.row_ptr, er.col) == "plain"
+    er = gen.er_csr(1 << 18, 1 << 21, seed=2)                      # mean degree 16
+    assert choose_hook(er.row_ptr, er.col) == "filtered"
+    assert choose_hook(er.row_ptr, er.col, symmetric=False) == "plain"
+    sparse = gen.er_csr(1 << 18, 1 << 19, seed=3)                  # mean degree 4
+    assert choose_hook(sparse.row_ptr, sparse.col) == "plain"
+    small = gen.er_csr(20_000, 200_000, seed=4)                     # small, mean degree 20
+    assert choose_hook(small.row_ptr, small.col) == "filtered"

@@ -73,7 +73,7 @@ __device__ __forceinline__ void dsm_hook(const DsmPi& d, int u, int v, int V, co
     const int H = ru > rv ? ru : rv;
     const int L = ru > rv ? rv : ru;
     const int old = d.cas(H, H, L);
-    if (old == H) return;
+    if (old == H || old == L) return;
     ru = dsm_find(d, old);
     rv = dsm_find(d, L);
     if (++guard > V) {

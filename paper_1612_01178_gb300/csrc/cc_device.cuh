@@ -211,7 +211,8 @@ __device__ __forceinline__ int find_root(int* pi, int x) {
 // Atomic-Hook of one edge (u, v) (Fig. 3, top; Section III-A). Both endpoints are walked to
 // their roots; while they differ, the higher root H is CASed from H (still a root) to the
 // lower one L. A failed CAS means another thread hooked H first; the walk resumes from the
-// value the CAS returned. The larger of the two roots strictly decreases on every retry, so
+// value the CAS returned, unless that value is L itself (H already hangs under L: done, which
+// spares the two walks when many threads hook the same pair of roots). The larger of the two roots strictly decreases on every retry, so
 // the loop ends within V retries; the guard only trips on corrupted memory.
 __device__ __forceinline__ void atomic_hook(int* pi, int u, int v, int V, const Ctl& c) {
   int ru = find_root(pi, u);
@@ -221,7 +222,7 @@ __device__ __forceinline__ void atomic_hook(int* pi, int u, int v, int V, const 
     const int H = ru > rv ? ru : rv;
     const int L = ru > rv ? rv : ru;
     const int old = atomicCAS(pi + H, H, L);
-    if (old == H) return;
+    if (old == H || old == L) return;
     ru = find_root(pi, old);
     rv = find_root(pi, L);
     if (++guard > V) {
@@ -314,7 +315,7 @@ __device__ __forceinline__ void atomic_hook_k(int* pi, const int (&u)[K], const 
     if (H[j] >= 0) old[j] = atomicCAS(pi + H[j], H[j], L[j]);
 #pragma unroll
   for (int j = 0; j < K; ++j)
-    if (H[j] >= 0 && old[j] != H[j]) atomic_hook(pi, old[j], L[j], V, c);
+    if (H[j] >= 0 && old[j] != H[j] && old[j] != L[j]) atomic_hook(pi, old[j], L[j], V, c);
 }
 
 // pi(v) <- v over [0, V), grid-strided; 16-byte stores when pi is 16-byte aligned.
@@ -494,7 +495,7 @@ __device__ __forceinline__ void local_hook(LT* lp, int a, int b) {
     const int H = ra > rb ? ra : rb;
     const int L = ra > rb ? rb : ra;
     const int old = cas_local(lp + H, H, L);
-    if (old == H) return;
+    if (old == H || old == L) return;
     ra = lfind(vlp, old);
     rb = lfind(vlp, L);
   }

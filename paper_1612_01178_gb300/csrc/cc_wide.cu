@@ -44,7 +44,7 @@ __device__ __forceinline__ void atomic_hook64(long long* pi, long long u, long l
     const long long L = ru > rv ? rv : ru;
     const long long old = (long long)atomicCAS(reinterpret_cast<unsigned long long*>(pi + H),
                                                (unsigned long long)H, (unsigned long long)L);
-    if (old == H) return;
+    if (old == H || old == L) return;
     ru = find_root64(pi, old);
     rv = find_root64(pi, L);
     if (++guard > V) {

@@ -160,26 +160,29 @@ __device__ __forceinline__ bool one_cta(const UnitInfo& ui, long long n_units) {
   return ui.single && (n_units >= (long long)gridDim.x || ui.nnz <= kOneCtaArcs);
 }
 
-// Fraction test of one window's locality by warp 0: the middle arc of 32 rows spread over the
-// window; true when the fraction f of sampled arcs that stay in the window is at least halfway
-// from what random endpoints would give (nrows / V_g) to 1: f >= (1 + nrows / V_g) / 2. For
-// large graphs that is one half; a graph of two windows needs three quarters, since random
-// arcs already stay in a window half the time there.
-__device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
+// Locality test of a multi-window graph by warp 0: the middle arc of 32 rows spread over the whole
+// graph (the same rows whichever window asks, so every window of a graph decides alike: a graph
+// whose windows disagreed would be neither filtered nor fully hooked in shared memory); true when
+// the fraction f of sampled arcs that stay in their row's window is at least halfway from what
+// random endpoints would give (W / V_g) to 1: f >= (1 + W / V_g) / 2. For large graphs that is one
+// half; a graph of two windows needs three quarters, since random arcs already stay in a window
+// half the time there.
+__device__ __forceinline__ bool graph_is_local(const UnitInfo& ui, int W) {
   const int lane = threadIdx.x & 31;
-  const int r = ui.w0 + (int)(((long long)lane * ui.nrows) / 32);
+  const int r = (int)(((long long)lane * ui.vg) / 32);
   bool sampled = false, local = false;
   const int a0 = ui.rp[r], a1 = ui.rp[r + 1];
   if (a0 >= 0 && a0 < a1 && (long long)a1 <= ui.nnz) {
     const int v = ui.col[a0 + (a1 - a0) / 2];
     if ((unsigned)v < (unsigned)ui.vg && v != r) {
       sampled = true;
-      local = (unsigned)(v - ui.w0) < (unsigned)ui.nrows;
+      local = v / W == r / W;
     }
   }
   const int ns = __popc(__ballot_sync(kFull, sampled));
   const int nl = __popc(__ballot_sync(kFull, local));
-  return 2ll * nl * ui.vg >= (long long)ns * ((long long)ui.vg + ui.nrows);
+  const long long w = (long long)W < (long long)ui.vg ? (long long)W : (long long)ui.vg;
+  return 2ll * nl * ui.vg >= (long long)ns * ((long long)ui.vg + w);
 }
 
 // ----- the sampled-and-filtered hook of the windows without locality (symmetric batches) -----
@@ -194,32 +197,68 @@ __device__ __forceinline__ bool window_is_local(const UnitInfo& ui) {
 // graph_hint value of a graph with a window hooked in phase A (never a vertex ID).
 constexpr int kMixedGraph = -2;
 
-// Rows [i0, i1) of window ui: the first kSampleArcs arcs of each, one row per thread.
+// Rows [i0, i1) of window ui: the first kSampleArcs arcs of each. A thread takes kHeadRows rows
+// (i, i + blockDim.x, ...) per step and hooks their arcs together, so the loads and root walks
+// of several rows are in flight at once: with one CTA per SM (the window's shared memory) a
+// thread has many rows to go through, and one row at a time left the phase bound on the
+// latency of each row's chain of dependent loads.
+constexpr int kHeadRows = 2;
 __device__ __forceinline__ void batched_row_heads(const Batch& b, const UnitInfo& ui, int i0, int i1, const Ctl& c) {
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const int u = ui.w0 + i;
-    int a0 = ui.rp[u], a1 = ui.rp[u + 1];
-    if (!(a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz)) {
-      raise_input_error(c, kSiteHookArc, (long long)ui.g);
-      if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
-      a1 = a0;
-    }
-    int uu[kSampleArcs], vv[kSampleArcs];
-    bool live[kSampleArcs];
+  constexpr int K = kHeadRows * kSampleArcs;
+  for (int i = i0 + threadIdx.x; i < i1; i += kHeadRows * blockDim.x) {
+    int uu[K], vv[K];
+    bool live[K];
 #pragma unroll
-    for (int j = 0; j < kSampleArcs; ++j) {
-      const bool has = (long long)a0 + j < (long long)a1;
-      const int v = has ? ld_stream(ui.col + a0 + j) : 0;
-      const bool in_range = (unsigned)v < (unsigned)ui.vg;
-      if (has && !in_range) {
-        raise_input_error(c, kSiteHookArc, (long long)ui.g);
-        if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+    for (int r = 0; r < kHeadRows; ++r) {
+      const int ir = i + r * (int)blockDim.x;
+      const int u = ui.w0 + ir;
+      int a0 = 0, a1 = 0;
+      if (ir < i1) {
+        a0 = ui.rp[u];
+        a1 = ui.rp[u + 1];
+        if (!(a0 >= 0 && a0 <= a1 && (long long)a1 <= ui.nnz)) {
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
+          if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+          a1 = a0;
+        }
       }
-      live[j] = has && in_range && v != u;
-      uu[j] = ui.vbase + u;
-      vv[j] = ui.vbase + v;
+#pragma unroll
+      for (int j = 0; j < kSampleArcs; ++j) {
+        const int k = r * kSampleArcs + j;
+        const bool has = (long long)a0 + j < (long long)a1;
+        const int v = has ? ld_stream(ui.col + a0 + j) : 0;
+        const bool in_range = (unsigned)v < (unsigned)ui.vg;
+        if (has && !in_range) {
+          raise_input_error(c, kSiteHookArc, (long long)ui.g);
+          if (b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
+        }
+        live[k] = has && in_range && v != u;
+        uu[k] = ui.vbase + u;
+        vv[k] = ui.vbase + v;
+      }
     }
-    atomic_hook_k<kSampleArcs>(b.labels, uu, vv, live, b.total_v, c);
+    atomic_hook_k<K>(b.labels, uu, vv, live, b.total_v, c);
+  }
+}
+
+// Multi-Jump (Fig. 3, bottom) of the vertices base + [i0, i1) of one window: a thread takes
+// kJumpVerts vertices (i, i + blockDim.x, ...) per step, whose parents and grandparents are
+// loaded together before each walk goes on alone, writing every step.
+constexpr int kJumpVerts = 4;
+__device__ __forceinline__ void batched_jump(int* labels, int base, int i0, int i1, int total_v, const Ctl& c) {
+  for (int i = i0 + threadIdx.x; i < i1; i += kJumpVerts * blockDim.x) {
+    int x[kJumpVerts], p[kJumpVerts], g[kJumpVerts];
+#pragma unroll
+    for (int j = 0; j < kJumpVerts; ++j) {
+      const int ij = i + j * (int)blockDim.x;
+      x[j] = base + ij;
+      p[j] = ij < i1 ? ld_pi(labels + x[j]) : x[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kJumpVerts; ++j) g[j] = p[j] != x[j] ? ld_pi(labels + p[j]) : p[j];
+#pragma unroll
+    for (int j = 0; j < kJumpVerts; ++j)
+      if (g[j] != p[j]) jump_from(labels, x[j], p[j], g[j], total_v, c);
   }
 }
 
@@ -325,7 +364,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       // is then hooked arc by arc in phase B, spread over all warps.
       bool local = true;
       if (!ui.single)
-        local = (c.window_mode == kWindowsPlain || n_units < (long long)gridDim.x) ? false : window_is_local(ui);
+        local = (c.window_mode == kWindowsPlain || n_units < (long long)gridDim.x) ? false : graph_is_local(ui, W);
       else if (!one_cta(ui, n_units))
         local = false;
       if (ui.nnz > 0x7fffffffLL) {  // graph too large for int32 row offsets: reported, not hooked
@@ -398,13 +437,8 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     for (unsigned long long item = blockIdx.x; item < n_plain * pparts; item += gridDim.x) {
       const UnitInfo ui = unit_info(b, b.plain_units[item / pparts], W);
       const long long part = (long long)(item % pparts);
-      const int base = ui.vbase + ui.w0;
-      const int i1 = split_point<int>(ui.nrows, (long long)pparts, part + 1);
-      for (int i = split_point<int>(ui.nrows, (long long)pparts, part) + threadIdx.x; i < i1; i += blockDim.x) {
-        const int x = base + i;
-        const int p = ld_pi(b.labels + x);
-        if (p != x) jump_from(b.labels, x, p, ld_pi(b.labels + p), b.total_v, c);
-      }
+      batched_jump(b.labels, ui.vbase + ui.w0, split_point<int>(ui.nrows, (long long)pparts, part),
+                   split_point<int>(ui.nrows, (long long)pparts, part + 1), b.total_v, c);
     }
     if (!grid_sync(c, epoch)) return;
     for (long long gw = tid >> 5; gw < b.n_graphs; gw += nt >> 5) {  // one warp per graph
@@ -516,14 +550,8 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       const UnitInfo ui = unit_info(b, (long long)(item / vparts), W);
       if (one_cta(ui, n_units)) continue;
       const long long part = (long long)(item % vparts);
-      const int base = ui.vbase + ui.w0;
-      const int i0 = split_point<int>(ui.nrows, (long long)vparts, part);
-      const int i1 = split_point<int>(ui.nrows, (long long)vparts, part + 1);
-      for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int x = base + i;
-        const int p = ld_pi(b.labels + x);
-        if (p != x) jump_from(b.labels, x, p, ld_pi(b.labels + p), b.total_v, c);
-      }
+      batched_jump(b.labels, ui.vbase + ui.w0, split_point<int>(ui.nrows, (long long)vparts, part),
+                   split_point<int>(ui.nrows, (long long)vparts, part + 1), b.total_v, c);
     }
     if (!grid_sync(c, epoch)) return;
   }
@@ -536,7 +564,15 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     const int base = ui.vbase + ui.w0;
     const int i0 = split_point<int>(ui.nrows, (long long)cparts, part);
     const int i1 = split_point<int>(ui.nrows, (long long)cparts, part + 1);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) b.labels[base + i] -= ui.vbase;
+    // four labels per thread and step, all loaded before any is stored
+    for (int i = i0 + threadIdx.x; i < i1; i += 4 * blockDim.x) {
+      int l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) l[j] = i + j * (int)blockDim.x < i1 ? b.labels[base + i + j * (int)blockDim.x] : 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i + j * (int)blockDim.x < i1) b.labels[base + i + j * (int)blockDim.x] = l[j] - ui.vbase;
+    }
   }
 }
 

@@ -87,11 +87,12 @@ enum {
 
 /* How the segment loop of Fig. 4 is driven on the device. */
 typedef enum cc_mode {
-  CC_MODE_AUTO = 0,        /* CC_MODE_PERSISTENT, except that a symmetric CSR (CC_FLAG_SYMMETRIC) of at
-                              least 2^17 vertices with no ID locality and skewed degrees (at least a
-                              quarter of the sampled rows below a quarter of the mean degree, as in
-                              power-law graphs), with tile_vertices = 0, runs CC_MODE_FILTERED;
-                              cc_last_run_info reports the mode that ran */
+  CC_MODE_AUTO = 0,        /* CC_MODE_PERSISTENT, except that a symmetric CSR (CC_FLAG_SYMMETRIC) with
+                              tile_vertices = 0 and no ID locality runs CC_MODE_FILTERED when its
+                              degrees are skewed (from 2^17 vertices: at least a quarter of the
+                              sampled rows below a quarter of the mean degree, as in power-law
+                              graphs) or its mean degree n_arcs / V is at least auto_dense_degree
+                              (8; any size); cc_last_run_info reports the mode that ran */
   CC_MODE_PERSISTENT = 1,  /* one cooperative launch; phases separated by grid barriers */
   CC_MODE_MULTI_LAUNCH = 2, /* host-driven (Section III): one init, then a Hook and a Multi-Jump launch per segment */
   /* The baselines the paper measures against (Section IV, Fig. 5), CSR only: the host loop of

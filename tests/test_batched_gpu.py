@@ -271,3 +271,25 @@ def test_million_vertex_graphs_among_small_ones(dev):
         got, st = run_batched(dev, b, status=True, flags=flags)
         assert (st == 0).all()
         assert_batch(got, b, want, what=f"flags={flags}")
+
+
+def test_window_boundary_sizes_with_many_windows(dev):
+    """Graphs of W - 1, W, W + 1, W + 232, 2W - 1 and 2W + 1 vertices (W = 32768, the batch window) of
+    both families, in a batch with more windows than CTAs, so each multi-window graph takes one hook
+    for all its windows from its locality sample (phase A for the grids, the sampled-and-filtered hook
+    for the ER graphs); every graph against the oracle, symmetric and not."""
+    W = 32768
+    graphs = []
+    for i, V in enumerate((W - 1, W, W + 1, W + 232, 2 * W - 1, 2 * W + 1)):
+        graphs.append(gen.er_csr(V, 6 * V, seed=800 + i))
+        side = int(np.ceil(np.sqrt(V)))
+        graphs.append(gen.grid_csr(side, 0.9, seed=820 + i))
+    for i in range(100):  # filler: 200 windows of ER graphs, so the batch has more windows than CTAs
+        graphs.append(gen.er_csr(40_000, 40_000 * (2 + i % 8), seed=840 + i))
+    order = np.random.default_rng(71).permutation(len(graphs))
+    b = gen.batch_from_graphs([graphs[i] for i in order])
+    want = expected(b)
+    for flags in (ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC, ccl.CC_FLAG_SYNC):
+        got, st = run_batched(dev, b, status=True, flags=flags)
+        assert (st == 0).all()
+        assert_batch(got, b, want, what=f"boundary sizes flags={flags}")

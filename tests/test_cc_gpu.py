@@ -246,6 +246,26 @@ def test_automatic_window_choice(dev):
         assert info["mode"] == mode, info
 
 
+def test_dense_degree_threshold(dev):
+    """auto_dense_degree sets the mean degree n_arcs / V from which a symmetric graph without ID
+    locality takes the sampled-and-filtered hook: -1 keeps the plain hook for a dense ER graph, a
+    threshold above its mean degree too, the default (8) and a lower one take the filter; the labels
+    are the oracle's every time. A value below -1 is refused."""
+    g = gen.er_csr(150_000, 1_500_000, seed=17)  # mean degree 20
+    want = expect(g.row_ptr, g.col)
+    rp, col = torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev)
+    for dense, mode in ((0, ccl.CC_MODE_FILTERED), (4, ccl.CC_MODE_FILTERED), (-1, ccl.CC_MODE_PERSISTENT),
+                        (32, ccl.CC_MODE_PERSISTENT)):
+        with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC,
+                                     auto_dense_degree=dense) as cc:
+            out = cc.csr(rp, col)
+            info = cc.run_info()
+        assert_labels(out.cpu().numpy(), want, f"auto_dense_degree={dense}")
+        assert info["mode"] == mode and info["tile_vertices"] == 0, (dense, info)
+    with pytest.raises(ccl.CCError):
+        ccl.ConnectedComponents(0, auto_dense_degree=-2)
+
+
 def test_grid_small_percolation(dev):
     for p in (0.3, 0.5, 0.7, 1.0):
         g = gen.grid_csr(700, p, seed=9)

@@ -49,6 +49,7 @@ struct Batch {
                                  // size (filled by the kernel)
   int* graph_hint;               // [n_graphs] giant-star root of each graph (filled by the kernel)
   int total_v;             // label arena size (batch-global IDs are below it)
+  int grid_a;              // CTAs of the first launch, whose count decided which graphs one CTA labels
   long long row_elems;     // descriptor mode: row-offset arena size
   long long arc_elems;     // descriptor mode: arc arena size
 };
@@ -156,8 +157,8 @@ __device__ __forceinline__ UnitInfo unit_info(const Batch& b, long long u, int W
 // while one walks all its arcs, so such a graph is hooked arc by arc on pi in phase B instead
 // (with batch-global IDs, like a window without locality).
 constexpr long long kOneCtaArcs = 8192;
-__device__ __forceinline__ bool one_cta(const UnitInfo& ui, long long n_units) {
-  return ui.single && (n_units >= (long long)gridDim.x || ui.nnz <= kOneCtaArcs);
+__device__ __forceinline__ bool one_cta(const UnitInfo& ui, long long n_units, int ctas) {
+  return ui.single && (n_units >= (long long)ctas || ui.nnz <= kOneCtaArcs);
 }
 
 // Locality test of a multi-window graph by warp 0: the middle arc of 32 rows spread over the whole
@@ -312,18 +313,17 @@ __device__ __forceinline__ void batched_rows_outside(const Batch& b, const UnitI
   }
 }
 
+// First launch (one CTA per SM: the window's parent array in shared memory): the unit table, then
+// phase A over every window.
 template <bool SYM>
-__device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ctl& c) {
+__device__ __forceinline__ void batched_front(const Batch& b, int* smem, const Ctl& c) {
   __shared__ long long s_warp_sums[32];
   __shared__ long long s_total;
   __shared__ unsigned long long s_unit;
   __shared__ int s_ovf, s_bad, s_plain;
-  __shared__ int s_warp_bad[kMaxBlockB / 32];
   if (launch_blocked(c)) return;
   unsigned epoch = 0;
   const int W = c.tile_w;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nt = (long long)gridDim.x * blockDim.x;
 
   // Windows per graph -> unit_start (block 0).
   if (blockIdx.x == 0) {
@@ -365,7 +365,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
       bool local = true;
       if (!ui.single)
         local = (c.window_mode == kWindowsPlain || n_units < (long long)gridDim.x) ? false : graph_is_local(ui, W);
-      else if (!one_cta(ui, n_units))
+      else if (!one_cta(ui, n_units, (int)gridDim.x))
         local = false;
       if (ui.nnz > 0x7fffffffLL) {  // graph too large for int32 row offsets: reported, not hooked
         local = true;
@@ -387,14 +387,14 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     } else {
       // A graph with a window hooked in phase A is not filtered: phase A drops the arcs with
       // v < u of a symmetric CSR, leaving them to the reverse arcs, which the filter may skip.
-      if (threadIdx.x == 0 && !one_cta(ui, n_units)) b.graph_hint[ui.g] = kMixedGraph;
+      if (threadIdx.x == 0 && !one_cta(ui, n_units, (int)gridDim.x)) b.graph_hint[ui.g] = kMixedGraph;
       if (ui.nnz <= 0x7fffffffLL)
         phase_a_window<int, SYM, int>(ui.rp, ui.col, ui.vg, (int)ui.nnz, ui.w0, ui.nrows, ui.vbase, lp, sink, &s_ovf,
                                  &s_bad, c);
       else
         __syncthreads();
       volatile int* vlp = lp;
-      if (one_cta(ui, n_units)) {
+      if (one_cta(ui, n_units, (int)gridDim.x)) {
         for (int i = threadIdx.x; i < ui.nrows; i += blockDim.x) b.labels[ui.vbase + i] = lfind(vlp, i);
       } else {
         const int base = ui.vbase + ui.w0;
@@ -408,7 +408,23 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     if (threadIdx.x == 0 && s_bad && b.graph_status) b.graph_status[ui.g] = kErrOutOfRange;
     __syncthreads();
   }
-  if (!grid_sync(c, epoch)) return;
+}
+
+// Second launch (no shared-memory window, so two 1024-thread CTAs per SM: twice the threads of the
+// first launch for phases bound by chains of dependent loads): the sampled-and-filtered hook of the
+// windows without locality, phase B, the Multi-Jumps and the relabelling. The first launch's
+// decisions reach it through global memory (unit table, worklist and window counters, labels).
+template <bool SYM>
+__device__ __forceinline__ void batched_back(const Batch& b, const Ctl& c) {
+  __shared__ long long s_warp_sums[32];
+  __shared__ long long s_total;
+  __shared__ int s_warp_bad[kMaxBlockB / 32];
+  if (launch_blocked(c)) return;
+  unsigned epoch = 0;
+  const int W = c.tile_w;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  const long long n_units = *reinterpret_cast<const volatile long long*>(b.unit_start + b.n_graphs);
 
   const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&c.st->counters[2]);
   const unsigned long long n_pairs = cur < c.wl_cap ? cur : c.wl_cap;
@@ -450,7 +466,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
         hint = kMixedGraph;  // matches no vertex: every row is read
       } else if (u1 > u0) {
         const UnitInfo ui = unit_info(b, u0, W);
-        if (!one_cta(ui, n_units)) {
+        if (!one_cta(ui, n_units, b.grid_a)) {
           const int x = ui.vbase + (int)(((long long)lane * ui.vg) / 32);
           const int val = ld_pi(b.labels + x);
           const unsigned grp = __match_any_sync(kFull, val);
@@ -548,7 +564,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
     const unsigned long long vparts = split_factor((unsigned long long)n_units, gridDim.x);
     for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * vparts; item += gridDim.x) {
       const UnitInfo ui = unit_info(b, (long long)(item / vparts), W);
-      if (one_cta(ui, n_units)) continue;
+      if (one_cta(ui, n_units, b.grid_a)) continue;
       const long long part = (long long)(item % vparts);
       batched_jump(b.labels, ui.vbase + ui.w0, split_point<int>(ui.nrows, (long long)vparts, part),
                    split_point<int>(ui.nrows, (long long)vparts, part + 1), b.total_v, c);
@@ -559,7 +575,7 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   const unsigned long long cparts = split_factor((unsigned long long)n_units, gridDim.x);
   for (unsigned long long item = blockIdx.x; item < (unsigned long long)n_units * cparts; item += gridDim.x) {
     const UnitInfo ui = unit_info(b, (long long)(item / cparts), W);
-    if (one_cta(ui, n_units)) continue;
+    if (one_cta(ui, n_units, b.grid_a)) continue;
     const long long part = (long long)(item % cparts);
     const int base = ui.vbase + ui.w0;
     const int i0 = split_point<int>(ui.nrows, (long long)cparts, part);
@@ -576,17 +592,47 @@ __device__ __forceinline__ void batched_body(const Batch& b, int* smem, const Ct
   }
 }
 
+// Phase timestamps (CC_FLAG_PHASE_TIMES): slot 0 the start, slot 1 the first launch's barrier, slot 2 the
+// end of phase A (the first launch's last block), then the second launch's barriers from slot 3.
+constexpr int kBatchedPhaseAEndSlot = 2;
+
 template <bool SYM>
 __global__ void __launch_bounds__(kMaxBlockB, 1) k_batched(Batch b, Ctl c) {
   extern __shared__ int dyn_smem[];
   if (c.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) c.phase_ns[0] = now_ns();
-  batched_body<SYM>(b, dyn_smem, c);
+  batched_front<SYM>(b, dyn_smem, c);
+  if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + kBatchedPhaseAEndSlot, now_ns());
+}
+
+template <bool SYM>
+__global__ void __launch_bounds__(kMaxBlockB, 2) k_batched_b(Batch b, Ctl c) {
+  batched_back<SYM>(b, c);
   if (c.phase_ns && threadIdx.x == 0) atomicMax(c.phase_ns + (c.phase_cap - 1), now_ns());
+}
+
+template <typename K>
+cudaError_t launch_cooperative(K k, LaunchShape s, size_t smem, cudaStream_t stream, const Batch& b, const Ctl& c) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)s.grid);
+  cfg.blockDim = dim3((unsigned)s.block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, b, c);
 }
 
 template <typename F>
 auto with_batched(bool sym, F&& f) {
   return sym ? f(k_batched<true>) : f(k_batched<false>);
+}
+
+template <typename F>
+auto with_batched_b(bool sym, F&& f) {
+  return sym ? f(k_batched_b<true>) : f(k_batched_b<false>);
 }
 
 }  // namespace
@@ -624,26 +670,38 @@ cudaError_t launch_batched(const BatchProblem& p, const Ctl& c, LaunchShape s, c
   b.plain_chunk_start = p.plain_chunk_start;
   b.graph_hint = p.graph_hint;
   b.total_v = (int)p.total_v;
+  b.grid_a = s.grid;
   b.row_elems = p.row_elems;
   b.arc_elems = p.arc_elems;
   const size_t smem = tiled_smem_bytes(c.tile_w, s.block);
-  return with_batched(p.sym, [&](auto k) {
+  cudaError_t e = with_batched(p.sym, [&](auto k) {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+      cudaError_t e1 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e1 != cudaSuccess) return e1;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)s.grid);
-    cfg.blockDim = dim3((unsigned)s.block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, b, c);
+    return launch_cooperative(k, s, smem, stream, b, c);
   });
+  if (e != cudaSuccess) return e;
+  // The second launch counts its grid barriers from zero again; its other status fields (work
+  // counters, worklist cursor) carry the first launch's results.
+  e = cudaMemsetAsync(&c.st->bar, 0, sizeof(c.st->bar), stream);
+  if (e != cudaSuccess) return e;
+  // Two CTAs per SM where the first launch fits one (the same SMs, scaled by the occupancy ratio).
+  const int per_sm_a = std::max(1, batched_blocks_per_sm(p.sym, s.block, c.tile_w));
+  const int per_sm_b = with_batched_b(p.sym, [&](auto k) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, s.block, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  });
+  if (per_sm_b <= 0) return cudaErrorInvalidConfiguration;
+  const LaunchShape sb{std::max(1, (int)((long long)s.grid * per_sm_b / per_sm_a)), s.block};
+  Ctl cb = c;
+  cb.phase_off = kBatchedPhaseAEndSlot;
+  cb.skip_arrival_block = -1;  // the test hook stops an arrival at the call's first barrier only
+  return with_batched_b(p.sym, [&](auto k) { return launch_cooperative(k, sb, 0, stream, b, cb); });
 }
 
 }  // namespace cc

@@ -338,7 +338,7 @@ void cc_destroy(cc_ctx* ctx);
    running inside a device memory allocator or pool, plug-ins whose host owns all
    device memory, or real-time paths that must not allocate).
    It needs no context and calls no cudaMalloc/cudaFree or allocating routine. The
-   only scratch the persistent kernel needs beyond the caller's arrays (its 72-byte
+   only scratch the persistent kernel needs beyond the caller's arrays (its 96-byte
    status block: grid-barrier counter, work counters and error word) lives in a
    static 256-byte device array inside libcc.so, held on every GPU that loads the
    library until the process exits; its size does not grow with the graph. It runs

@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = 256;  // the stated maximum: one status block (sizeof(DevStatus) = 72 bytes used)
+constexpr size_t kScratchBytes = 256;  // the stated maximum: one status block (sizeof(DevStatus) = 96 bytes used)
 static_assert(sizeof(cc::DevStatus) <= kScratchBytes, "status block must fit the static scratch");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

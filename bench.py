@@ -509,12 +509,13 @@ def run_batched(args, rank, world, local_rank):
                            "speedup_of_batched": bg_ms / ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": peak_kind, "bytes_alg_per_launch": b_alg,
-                     "kernel": "k_batched<SYM>", "kernel_ms_mean": ms},
+                     "kernel": "k_batched<SYM> + k_batched_b<SYM> (one labelling, both launches)",
+                     "kernel_ms_mean": ms},
         "cpu_baseline": {"value": cpu_graphs / cpu_t if cpu_t else None, "unit": "graphs/s", "cores": 1,
                          "kind": "oracle", "edges_per_s": (cpu_arcs // 2) / cpu_t if cpu_t else None,
                          "sample": f"{cpu_graphs} sampled graphs of the batch ({cpu_arcs} arcs), union-find oracle, "
                                    "1 host thread"},
-        "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps, "parity": parity,
+        "e2e": e2e, "clocks": clocks, "gpu_launches": info["launches"] * args.steps, "parity": parity,
     }
     print(json.dumps(line), flush=True)
     cc.close()

@@ -825,7 +825,7 @@ static cc_status run_batch(cc_ctx* ctx, cc::BatchProblem& p, long long total_arc
   info.segments = o.segments;
   info.grid_blocks = (int)grid;
   info.block = block;
-  info.launches = 1;
+  info.launches = 2;  // phase A with the window in shared memory, then the rest (cc_batched.cu)
   info.tile_vertices = W;
   info.worklist_capacity = (int64_t)ctx->d_wl_pairs;
   ctx->last = info;

@@ -293,3 +293,15 @@ def test_window_boundary_sizes_with_many_windows(dev):
         got, st = run_batched(dev, b, status=True, flags=flags)
         assert (st == 0).all()
         assert_batch(got, b, want, what=f"boundary sizes flags={flags}")
+
+
+def test_batched_reports_two_launches(dev):
+    """A batched labelling is two launches (phase A with the window in shared memory, then the
+    rest), and the run info says so."""
+    b = gen.batch_from_graphs([gen.er_csr(5000, 20_000, seed=91), gen.grid_csr(100, 0.9, seed=92)])
+    with ccl.ConnectedComponents(0, flags=ccl.CC_FLAG_SYNC | ccl.CC_FLAG_SYMMETRIC) as cc:
+        v_off, a_off, rp, col = to_dev(dev, b)
+        out = cc.batched(v_off, a_off, rp, col)
+        info = cc.run_info()
+    assert info["launches"] == 2, info
+    assert_batch(out.cpu().numpy(), b, what="two launches")

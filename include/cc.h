@@ -175,7 +175,11 @@ void cc_default_options(cc_options* opt);
 
 /* Creates a context on `device`. `stream` is a cudaStream_t to issue work on
    (NULL = the legacy default stream). `opt` may be NULL (defaults). Allocates a
-   small device status block and a pinned host mirror of it. */
+   small device status block and a pinned host mirror of it. The context holds the
+   state that Section III keeps on the device so that the segment loop of Fig. 4 runs
+   without host round trips: the grid-barrier counter, the work counters and the
+   error words of the status block. Returns CC_ERR_INVALID_ARG for bad options,
+   CC_ERR_CUDA or CC_ERR_OOM when the device or the allocation fails. */
 cc_status cc_create(cc_ctx** out, int device, void* stream, const cc_options* opt);
 
 /* Replaces the stream / options of a context. */
@@ -214,11 +218,17 @@ cc_status cc_labels_csr(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const v
 cc_status cc_labels_csr64(cc_ctx* ctx, int64_t n_vertices, int64_t n_arcs, const int64_t* row_ptr,
                           const int64_t* col_idx, int64_t* labels);
 
-/* Connected components of an edge list (COO): edge i joins src[i] and dst[i].
+/* Connected components of an edge list (COO): edge i joins src[i] and dst[i]. The
+ * graph of Section II given by its edge set E, labelled with Fig. 4 over E: each
+ * edge is Atomic-Hooked once (Fig. 3, top), each of the s edge segments followed by
+ * a Multi-Jump (Fig. 3, bottom).
  *   src, dst    device int32 [n_edges], values in [0, V); each edge is undirected
  *               and is hooked once.
- *   labels      device int32 [V], caller-owned output.
- * s defaults to max(1, round(2 n_edges / V)). */
+ *   labels      device int32 [V], caller-owned output (min-ID labels).
+ * Segments: cc_options.segments; 0 = 4 when 2 n_edges / V < 3, else 1 (the GB300
+ * measurement of Fig. 6); -1 = the paper's max(1, round(2 n_edges / V)) (Section
+ * III-B counts |E| edges, two arcs each). An endpoint outside [0, V) is skipped and
+ * reported as CC_ERR_OUT_OF_RANGE; the inputs are not modified. */
 cc_status cc_labels_coo(cc_ctx* ctx, int64_t n_vertices, int64_t n_edges, const int32_t* src,
                         const int32_t* dst, int32_t* labels);
 
@@ -329,8 +339,9 @@ const char* cc_last_error_message(const cc_ctx* ctx);
 /* Static description of a status code. */
 const char* cc_status_string(cc_status status);
 
-/* Releases the context and everything it allocated. NULL is ignored. Waits for
-   the context's stream first. */
+/* Releases the context and everything it allocated (the device state of
+   cc_create, worklist and staging buffers). NULL is ignored. Waits for the
+   context's stream first. */
 void cc_destroy(cc_ctx* ctx);
 
 /* Allocation-free variant of cc_labels_csr (the paper has no counterpart: this
